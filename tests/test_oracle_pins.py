@@ -1,0 +1,341 @@
+"""Pins of the oracle's time step against what the paper and the mathematics
+fix, independently of the oracle's own formulas:
+
+* equilibrium and force against the Hermite expansion of Eq. equi.hermite and
+  of the force (numpy's probabilists' Hermite polynomials, tensor indices
+  enumerated one by one);
+* equilibrium moments against the closed forms of Eq. ce.11, ce.13, ce.18;
+* force moments: zero mass, momentum rho g (used under Eq. nm.10), second
+  moment rho (g u + u g);
+* collision: exact mass conservation (Sect. III, BGK) and the momentum
+  impulse dt rho g per step implied by Eq. nm.8 and nm.10;
+* streaming + walls: a push-style brute force of the same step, exact mass
+  conservation, zero net flux per wall column (Eq. Psi), the rest state as a
+  fixed point, mirror symmetry of the channel;
+* steady Poiseuille flow: Psi -> 1 (Sect. V), the Navier-Stokes curvature
+  g/nu with nu = tau (Eq. nm.11) as the grid is refined, mdot -> 1/(6 Kn)
+  (Eq. pf.2) as Kn -> 0, and a Newton solve of the fixed point on a tiny grid.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from numpy.polynomial import hermite_e as He
+
+import oracle
+from lbm_inputs import DVM_TABLES, rho_field
+from oracle import dvm
+
+SETS = [("D2V16", 3), ("D2V33", 4), ("D2V32", 3), ("D3V107xz", 3), ("D2V16", 4),
+        ("D2V33", 3), ("D2V16", 2)]
+
+
+def _chan(name, N, Nx=3, Ny=8, Kn=0.1, g=None):
+    if g is None:
+        g = oracle.force_for_mach(Kn, 3e-2)
+    return oracle.channel(name, N, Nx, Ny, Kn, g)
+
+
+def _He_tensor(xi, idx):
+    """H^(n)_{i1..in}(xi) for the Gaussian weight: the product over axes of
+    1D probabilists' Hermite polynomials He_{n_d}(xi_d), n_d = number of
+    indices equal to d."""
+    out = 1.0
+    for d in range(2):
+        nd = sum(1 for i in idx if i == d)
+        out = out * He.hermeval(xi[d], [0] * nd + [1])
+    return out
+
+
+def _hermite_series(coefs, xi):
+    """sum_n (1/n!) a^(n)_{i1..in} H^(n)_{i1..in}(xi), indices enumerated."""
+    tot = 0.0
+    for n, a in enumerate(coefs):
+        for idx in itertools.product(range(2), repeat=n):
+            tot += a(idx) * _He_tensor(xi, idx) / math.factorial(n)
+    return tot
+
+
+@pytest.mark.parametrize("name,N", SETS)
+def test_equilibrium_is_hermite_expansion(name, N):
+    """Eq. equi.hermite with a^(n) = rho u...u (Eq. equi.hermite.coef)."""
+    ch = _chan(name, N)
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        rho = 1 + 0.1 * rng.standard_normal()
+        u = 0.05 * rng.standard_normal(2)
+        f0 = ch.equilibrium(rho, u[0], u[1])
+        coefs = [lambda idx, n=n: rho * np.prod([u[i] for i in idx]) for n in range(N + 1)]
+        for a in range(ch.V):
+            xi = ch.c * np.array([ch.ex[a], ch.ey[a]], dtype=float)
+            ref = ch.w[a] * _hermite_series(coefs, xi)
+            assert abs(f0[a] - ref) <= 1e-14 * max(1.0, abs(ref) / ch.w[a]) * ch.w[a] * 10
+
+
+@pytest.mark.parametrize("name,N", SETS)
+def test_force_is_hermite_expansion(name, N):
+    """Eq. nm.4 = w [rho g.H1 + (1/2) rho (g u + u g):H2 + (1/6) b3:H3],
+    b3_ijk = g_i A_jk + g_j A_ik + g_k A_ij, A = Pi - rho delta (N >= 3)."""
+    ch = _chan(name, N, g=0.0)
+    rng = np.random.default_rng(2)
+    g = np.array([0.02, -0.01])
+    ch.p.gx, ch.p.gy = g
+    for _ in range(3):
+        rho = 1 + 0.1 * rng.standard_normal()
+        u = 0.05 * rng.standard_normal(2)
+        Pi = rho * np.eye(2) + 0.05 * rng.standard_normal((2, 2))
+        Pi = 0.5 * (Pi + Pi.T)
+        A = Pi - rho * np.eye(2)
+        F = ch.force(rho, u[0], u[1], Pi)
+        coefs = [lambda idx: 0.0,
+                 lambda idx: rho * g[idx[0]],
+                 lambda idx: rho * (g[idx[0]] * u[idx[1]] + u[idx[0]] * g[idx[1]])]
+        if N >= 3:
+            coefs.append(lambda idx: (g[idx[0]] * A[idx[1], idx[2]] + g[idx[1]] * A[idx[0], idx[2]]
+                                      + g[idx[2]] * A[idx[0], idx[1]]))
+        for a in range(ch.V):
+            xi = ch.c * np.array([ch.ex[a], ch.ey[a]], dtype=float)
+            ref = ch.w[a] * _hermite_series(coefs, xi)
+            assert abs(F[a] - ref) <= 1e-13 * ch.w[a]
+
+
+def _sym_delta_u(u, i, j, k):
+    d = np.eye(2)
+    return u[i] * d[j, k] + u[j] * d[i, k] + u[k] * d[i, j]
+
+
+@pytest.mark.parametrize("name,N", SETS)
+def test_equilibrium_moments_closed_forms(name, N):
+    """Sum_a f0 xi^k: rho, rho u, rho (delta + u u) (Eq. ce.11), and for N >= 3
+    rho (u u u + sym(u delta)) (Eq. ce.13); exact while k + N <= Q."""
+    ch = _chan(name, N)
+    Q = dvm.quadrature_order(np.stack([ch.ex, ch.ey], 1), ch.w, ch.c)
+    rho, u = 1.03, np.array([0.04, -0.02])
+    f0 = ch.equilibrium(rho, *u)
+    xi = ch.c * np.stack([ch.ex, ch.ey], 1).astype(float)
+    assert abs(f0.sum() - rho) < 1e-14
+    assert np.allclose(f0 @ xi, rho * u, atol=1e-15, rtol=0)
+    M2 = np.einsum("a,ai,aj->ij", f0, xi, xi)
+    assert np.allclose(M2, rho * (np.eye(2) + np.outer(u, u)), atol=1e-14, rtol=0)
+    if N >= 3 and N + 3 <= Q:
+        M3 = np.einsum("a,ai,aj,ak->ijk", f0, xi, xi, xi)
+        for i, j, k in itertools.product(range(2), repeat=3):
+            ref = rho * (u[i] * u[j] * u[k] + _sym_delta_u(u, i, j, k))
+            assert abs(M3[i, j, k] - ref) < 1e-13
+    if N >= 4 and N + 4 <= Q:
+        # Eq. ce.18 for theta = 1: rho (uuuu + sym(uu delta) + sym(delta delta))
+        M4 = np.einsum("a,ai,aj,ak,al->ijkl", f0, xi, xi, xi, xi)
+        d = np.eye(2)
+        for i, j, k, l in itertools.product(range(2), repeat=4):
+            uu_d = (u[i] * u[j] * d[k, l] + u[i] * u[k] * d[j, l] + u[i] * u[l] * d[j, k]
+                    + u[j] * u[k] * d[i, l] + u[j] * u[l] * d[i, k] + u[k] * u[l] * d[i, j])
+            dd = d[i, j] * d[k, l] + d[i, k] * d[j, l] + d[i, l] * d[j, k]
+            ref = rho * (u[i] * u[j] * u[k] * u[l] + uu_d + dd)
+            assert abs(M4[i, j, k, l] - ref) < 1e-13
+
+
+@pytest.mark.parametrize("name,N", SETS)
+def test_force_moments(name, N):
+    ch = _chan(name, N, g=0.0)
+    g = np.array([0.01, 0.003])
+    ch.p.gx, ch.p.gy = g
+    rho, u = 0.98, np.array([0.03, 0.01])
+    Pi = np.array([[1.1, 0.02], [0.02, 0.95]])
+    F = ch.force(rho, *u, Pi)
+    xi = ch.c * np.stack([ch.ex, ch.ey], 1).astype(float)
+    assert abs(F.sum()) < 1e-15
+    assert np.allclose(F @ xi, rho * g, atol=1e-15, rtol=0)
+    M2 = np.einsum("a,ai,aj->ij", F, xi, xi)
+    assert np.allclose(M2, rho * (np.outer(g, u) + np.outer(u, g)), atol=1e-14, rtol=0)
+
+
+def _random_state(ch, seed, amp=0.02):
+    rng = np.random.default_rng(seed)
+    return ch.w[:, None, None] * (1 + amp * rng.standard_normal((ch.V, ch.Ny, ch.Nx)))
+
+
+@pytest.mark.parametrize("name,N", SETS)
+def test_collision_conserves_mass_and_adds_force_impulse(name, N):
+    """Eq. nm.8: sum fbar* = sum fbar; sum fbar* xi = sum fbar xi + dt rho g;
+    second moment relaxes: (1-omega) Pibar + omega rho(delta + uu + tau(gu+ug))."""
+    ch = _chan(name, N, Kn=0.05)
+    f = _random_state(ch, 3)
+    fs = ch.collide(f)
+    rho, ux, uy = ch.moments(f)
+    xi = ch.c * np.stack([ch.ex, ch.ey], 1).astype(float)
+    assert np.allclose(fs.sum(0), f.sum(0), rtol=0, atol=2e-15)
+    jx0 = np.einsum("ayx,a->yx", f, xi[:, 0])
+    jx1 = np.einsum("ayx,a->yx", fs, xi[:, 0])
+    assert np.allclose(jx1 - jx0, ch.dt * rho * ch.g, rtol=0, atol=5e-16)
+    om, tau, g = ch.omega, ch.tau, np.array([ch.g, 0.0])
+    for (y, x) in [(0, 0), (3, 1), (7, 2)]:
+        u = np.array([ux[y, x], uy[y, x]])
+        Pb = np.einsum("a,ai,aj->ij", f[:, y, x], xi, xi)
+        Ps = np.einsum("a,ai,aj->ij", fs[:, y, x], xi, xi)
+        r = rho[y, x]
+        ref = (1 - om) * Pb + om * r * (np.eye(2) + np.outer(u, u)
+                                         + tau * (np.outer(g, u) + np.outer(u, g)))
+        assert np.allclose(Ps, ref, rtol=0, atol=1e-14)
+
+
+def _push_stream(ch, fs):
+    """Brute force of streaming + diffuse walls written push-style: move
+    every packet to its target node; a packet that leaves the channel puts
+    its mass into the bucket of the wall column where it lands; each bucket
+    is re-emitted as Psi rho_w w_a into the |e_y| rows of every incoming a."""
+    V, Ny, Nx = fs.shape
+    out = np.full_like(fs, np.nan)
+    bucket = {"bot": np.zeros(Nx), "top": np.zeros(Nx)}
+    for a in range(V):
+        for y in range(Ny):
+            for x in range(Nx):
+                tx, ty = (x + ch.ex[a]) % Nx, y + ch.ey[a]
+                if ty < 0:
+                    bucket["bot"][tx] += fs[a, y, x]
+                elif ty >= Ny:
+                    bucket["top"][tx] += fs[a, y, x]
+                else:
+                    out[a, ty, tx] = fs[a, y, x]
+    emit_bot = sum(ch.ey[a] * ch.w[a] for a in range(V) if ch.ey[a] > 0)
+    emit_top = sum(-ch.ey[a] * ch.w[a] for a in range(V) if ch.ey[a] < 0)
+    for a in range(V):
+        for x in range(Nx):
+            for r in range(abs(ch.ey[a])):
+                if ch.ey[a] > 0:
+                    out[a, r, x] = bucket["bot"][x] / emit_bot * ch.w[a]
+                elif ch.ey[a] < 0:
+                    out[a, Ny - 1 - r, x] = bucket["top"][x] / emit_top * ch.w[a]
+    assert not np.isnan(out).any()
+    return out, bucket
+
+
+@pytest.mark.parametrize("name,N", SETS[:4])
+@pytest.mark.parametrize("Nx,Ny", [(1, 12), (5, 9), (7, 13)])
+def test_stream_matches_push_brute_force(name, N, Nx, Ny):
+    ch = _chan(name, N, Nx=Nx, Ny=max(Ny, max(abs(dvm.dvm2d(name, DVM_TABLES)[0][:, 1]))))
+    fs = _random_state(ch, 4)
+    f = ch.stream(fs)
+    ref, bucket = _push_stream(ch, fs)
+    assert np.allclose(f, ref, rtol=0, atol=1e-16)
+    # exact mass conservation and zero net flux per wall column
+    assert abs(f.sum() - fs.sum()) < 1e-13 * fs.sum()
+    for x in range(ch.Nx):
+        inflow = sum(f[a, r, x] for a in range(ch.V) if ch.ey[a] > 0 for r in range(ch.ey[a]))
+        assert abs(inflow - bucket["bot"][x]) < 1e-14 * abs(bucket["bot"][x])
+
+
+@pytest.mark.parametrize("name,N", SETS[:4])
+def test_rest_state_is_fixed_point(name, N):
+    ch = _chan(name, N, Nx=2, Ny=16, g=0.0).init()
+    ch.step(500)
+    assert np.max(np.abs(ch.f - ch.w[:, None, None])) < 1e-14
+
+
+def test_mass_conserved_over_many_steps():
+    ch = oracle.channel("D2V33", 4, 16, 24, 0.1, oracle.force_for_mach(0.1))
+    ch.init(rho_field(16, 24, seed=7))
+    m0 = ch.f.sum()
+    ch.step(2000)
+    assert abs(ch.f.sum() - m0) < 1e-13 * m0
+
+
+@pytest.mark.parametrize("name,N", SETS[:4])
+def test_channel_mirror_symmetry(name, N):
+    Kn = 0.2
+    ch = oracle.channel(name, N, 1, 32, Kn, oracle.force_for_mach(Kn)).init()
+    ch.step(400)
+    u = ch.moments()[1][:, 0]
+    assert np.max(np.abs(u - u[::-1])) < 1e-12 * np.max(np.abs(u))
+
+
+def _psi_rho_w(ch):
+    """Psi rho_w of the bottom wall for the current state (Eq. nm.15)."""
+    fs = ch.collide(ch.f)
+    out = sum(fs[a, j, 0] for a in range(ch.V) if ch.ey[a] < 0 for j in range(-ch.ey[a]))
+    den = sum(ch.ey[a] * ch.w[a] for a in range(ch.V) if ch.ey[a] > 0)
+    return out / den
+
+
+def test_steady_poiseuille_psi_is_one():
+    """Steady unidirectional flow at uniform density has Psi = 1 (Sect. V)."""
+    Kn = 0.1
+    ch = oracle.channel("D2V16", 3, 1, 64, Kn, oracle.force_for_mach(Kn)).init()
+    conv, steps, du = ch.run_to_steady(1e-12, 50000)
+    assert conv
+    rho = ch.moments()[0]
+    assert abs(_psi_rho_w(ch) / rho[0, 0] - 1.0) < 1e-5
+
+
+def test_navier_stokes_curvature_second_order():
+    """Interior profile curvature -> g/nu with nu = tau (Eq. nm.11, nm.8's
+    trapezoidal scheme has no dt/2 viscosity shift); error O(dx^2)."""
+    Kn = 0.02
+    errs = []
+    for Ny in (32, 64):
+        ch = oracle.channel("D2V16", 3, 1, Ny, Kn, oracle.force_for_mach(Kn)).init()
+        conv, _, _ = ch.run_to_steady(1e-12, 100000)
+        assert conv
+        u = ch.moments()[1][:, 0]
+        z = (np.arange(Ny) + 0.5) / Ny - 0.5
+        A = np.stack([np.ones(Ny), 1 - 4 * z ** 2], 1)
+        b = np.linalg.lstsq(A, u, rcond=None)[0][1]
+        errs.append(abs(b * 8 * ch.tau / ch.g - 1))
+    assert errs[1] < 5e-3
+    assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_mass_flow_navier_stokes_limit():
+    """Eq. pf.2: mdot -> 1/(6 Kn) as Kn -> 0, the difference tending to a
+    constant (the slip contribution)."""
+    vals = []
+    for Kn in (0.02, 0.01):
+        ch = oracle.channel("D2V16", 3, 1, 64, Kn, oracle.force_for_mach(Kn)).init()
+        conv, _, _ = ch.run_to_steady(1e-12, 100000)
+        assert conv
+        vals.append(ch.mass_flow() - 1 / (6 * Kn))
+    assert abs(vals[0] - vals[1]) < 0.05
+    assert 0.5 < vals[1] < 2.0
+
+
+def test_wall_exact_model_near_dsmc():
+    """Sect. VI.B: S3 models (sigma_zxx = 0) agree with DSMC mass flow; the
+    paper quotes mdot_DSMC = 1.76 at Kn = 0.4514.  The (x, z) marginal of
+    D3V107 is exact for the paper's y-uniform channel."""
+    Kn = 0.4514
+    ch = oracle.channel("D3V107xz", 3, 1, 64, Kn, oracle.force_for_mach(Kn)).init()
+    conv, _, _ = ch.run_to_steady(1e-11, 50000)
+    assert conv
+    assert abs(ch.mass_flow() / 1.76 - 1) < 0.03
+
+
+def test_fixed_point_by_newton_on_tiny_grid():
+    """The time-marched steady state equals the fixed point f = S(C(f)) found
+    by Newton's method with a finite-difference Jacobian (total mass fixed)."""
+    Kn = 0.3
+    ch = oracle.channel("D2V16", 3, 1, 8, Kn, oracle.force_for_mach(Kn, 1e-2)).init()
+    conv, _, _ = ch.run_to_steady(1e-15, 100000, check_every=50)
+    assert conv
+    marched = ch.moments()[1][:, 0].copy()
+
+    ch2 = oracle.channel("D2V16", 3, 1, 8, Kn, oracle.force_for_mach(Kn, 1e-2)).init()
+    x = ch2.f.ravel().copy()
+    M0 = x.sum()
+
+    def resid(v):
+        fs = ch2.collide(v.reshape(ch2.f.shape))
+        r = ch2.stream(fs).ravel() - v
+        r[0] = v.sum() - M0          # replace one equation by the mass constraint
+        return r
+
+    for _ in range(8):
+        r = resid(x)
+        J = np.empty((x.size, x.size))
+        h = 1e-7
+        for k in range(x.size):
+            xp = x.copy()
+            xp[k] += h
+            J[:, k] = (resid(xp) - r) / h
+        x = x - np.linalg.solve(J, r)
+    newton = ch2.moments(x.reshape(ch2.f.shape))[1][:, 0]
+    assert np.max(np.abs(newton - marched)) < 1e-9 * np.max(np.abs(marched))
