@@ -1,0 +1,357 @@
+"""Benchmark: lattice-cell updates per second of the fused stream-collide step
+on the channel workload D2V33 (S^{D2V33}_{Q9E132}), Hermite order 4,
+Nx = 4096 periodic x Ny = 512 between diffuse walls, seeded density
+1 + 1e-3 N(0, 1), body force for Ma ~ 1e-3.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One benchmark step = --lb-steps (default 1000) lattice-Boltzmann time steps,
+one kernel launch each.  `value` is device-resident throughput (GLUPS) over K
+steps timed with CUDA events on the solver's stream; `e2e` is the same metric
+through the C ABI with the density field copied from pinned host memory and
+the mass flow read back every step.  With N > 1 (torchrun) every rank runs
+its own channel (independent replicas, weak scaling); rank 0 prints one JSON
+line.  `--impl reference` times the fp64 CPU oracle instead (rank 0 only).
+"""
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GLUPS & %HBM roofline"
+UNIT = "GLUPS"
+DVM, ORDER, NX, NY, SEED = "D2V33", 4, 4096, 512, 20151029
+WORKLOAD = ("channel D2V33 (S^{D2V33}_{Q9E132}), Hermite order 4, Nx=4096 periodic x "
+            "Ny=512 diffuse Maxwell walls, rho=1+1e-3 N(0,1) seed 20151029, Ma~1e-3 force")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--lb-steps", type=int, default=1000)
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--kn", type=float, default=0.1)
+    p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1510_08886_gb300", "csrc")
+    for fn in ("lbm_kernels.cuh", "lbm_internal.h", "k_fp32.cu", "k_fp64.cu"):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(precision):
+    """DRAM bytes per launch from the committed ncu summary of this kernel,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"stream_collide_{precision}_D2V33_4096x512.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    hsh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not hsh or hsh.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(precision, Kn):
+    """The fp64 oracle as it stands, single-threaded, one full-size time step
+    of the benchmark workload (collision + streaming + walls)."""
+    import oracle
+    from lbm_inputs import rho_field
+    ch = oracle.channel(DVM, ORDER, NX, NY, Kn, oracle.force_for_mach(Kn))
+    ch.init(rho_field(NX, NY, seed=SEED))
+    t0 = time.perf_counter()
+    ch.step(1)
+    dt = time.perf_counter() - t0
+    return {"value": NX * NY / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 time step of the full {NX}x{NY} workload, fp64 C oracle, "
+                      f"1 thread ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from lbm_inputs import rho_field
+    # each step: one time step of a 512-column slab of the workload (all 512
+    # rows, both walls), the oracle as it stands, 1 thread
+    cols = 512
+    rho = rho_field(NX, NY, seed=SEED)[:, :cols]
+    ch = oracle.channel(DVM, ORDER, cols, NY, args.kn, oracle.force_for_mach(args.kn)).init(rho)
+    for _ in range(args.warmup):
+        ch.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ch.step(1)
+    dt = time.perf_counter() - t0
+    v = cols * NY * args.steps / dt / 1e9
+    sample = f"1 time step of a {cols}-column x {NY}-row slab per step, fp64 C oracle, 1 thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lb_steps_per_step": 1, "sample_cells": cols * NY,
+                   "parallelism": "single host thread"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_1510_08886_gb300 as lbm
+    from paper_1510_08886_gb300 import _lib
+    from lbm_inputs import rho_field
+
+    e, w, c = lbm.dvm(DVM)
+    V = len(w)
+    ncell = NX * NY
+    g = lbm.force_for_mach(args.kn)
+    stream = torch.cuda.Stream()
+    rho_host = rho_field(NX, NY, seed=SEED + rank)
+    rho_dev = torch.tensor(rho_host, device="cuda")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_run(precision, Kn, lb, steps, warmup, sample_clocks=False):
+        s = lbm.Solver(e, w, c, ORDER, NX, NY, Kn, lbm.force_for_mach(Kn), precision=precision,
+                       stream=stream)
+        s.init(rho_dev)
+        for _ in range(warmup):
+            s.step(lb)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.__enter__()
+        ev0.record(stream)
+        for _ in range(steps):
+            s.step(lb)
+        ev1.record(stream)
+        ev1.synchronize()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        st = s.status()
+        mdot = s.mass_flow()
+        s.close()
+        return ms, (sampler.summary() if sampler else None), st, mdot
+
+    # ---- headline: device-resident throughput ------------------------------
+    ms, clocks, status, mdot = timed_run(args.precision, args.kn, args.lb_steps, args.steps,
+                                         args.warmup, sample_clocks=True)
+    ms_t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    launches = args.steps * args.lb_steps
+    value = ws * ncell * launches / (ms_max * 1e-3) / 1e9
+    elem = 4 if args.precision == "fp32" else 8
+    bytes_per_launch = 2 * V * elem * ncell          # read + write every population once
+    avg_launch_s = ms * 1e-3 / launches
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    traffic = ncu_traffic(args.precision)
+
+    # ---- e2e through the C ABI with host buffers ---------------------------
+    pinned = torch.empty((NY, NX), dtype=torch.float64, pin_memory=True)
+    pinned.numpy()[:] = rho_host
+    s = lbm.Solver(e, w, c, ORDER, NX, NY, args.kn, g, precision=args.precision, stream=stream)
+    L = _lib.lib()
+    res = np.zeros(2)
+    host_ptr = ctypes.cast(pinned.data_ptr(), _lib.c_double_p)
+    mptr = res.ctypes.data_as(_lib.c_double_p)
+
+    def e2e_step():
+        _lib.check(L.lbm_init(s.handle, host_ptr), "lbm_init")
+        _lib.check(L.lbm_step(s.handle, args.lb_steps), "lbm_step")
+        _lib.check(L.lbm_mass_flow(s.handle, mptr, None), "lbm_mass_flow")
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    ev1.record(stream)
+    ev1.synchronize()
+    wall = time.perf_counter() - t0
+    e2e_ms = wall * 1e3          # host wall clock: copies, launches and reads included
+    s.close()
+    e2e_t = torch.tensor([e2e_ms], device="cuda")
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = ws * ncell * args.steps * args.lb_steps / (float(e2e_t.item()) * 1e-3) / 1e9
+
+    # ---- variants: both precisions, Kn in {0.01, 0.1, 1.0} -----------------
+    variants = []
+    if not args.no_variants:
+        for prec in ("fp64", "fp32"):
+            for Kn in (0.01, 0.1, 1.0):
+                lb = 200
+                vms, _, vst, vm = timed_run(prec, Kn, lb, 1, 1)
+                el = 4 if prec == "fp32" else 8
+                variants.append({
+                    "precision": prec, "Kn": Kn, "lb_steps": lb,
+                    "GLUPS": ncell * lb / (vms * 1e-3) / 1e9,
+                    "achieved_GBs": 2 * V * el * ncell * lb / (vms * 1e-3) / 1e9,
+                    "mdot": vm, "status": vst})
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.precision, args.kn)
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "Kn": args.kn, "lb_steps_per_step": args.lb_steps,
+                       "cells": ncell, "velocities": V,
+                       "storage": ("fp32 deviations fbar - w" if args.precision == "fp32"
+                                   else "fp64 deviations fbar - w"),
+                       "l2": "inputs larger than L2 (two lattices of "
+                             f"{V * elem * ncell / 1e6:.0f} MB each)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind,
+                         "kernel": "k_step<R=1,P=16,N=4> (fused pull-stream + walls + collide)",
+                         "bytes_per_launch": bytes_per_launch,
+                         "avg_launch_us": avg_launch_s * 1e6},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": ncell * 8,
+                    "d2h_bytes_per_step": 4 * 8 + 4},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "status": status, "mdot": mdot,
+            "variants": variants,
+        }))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

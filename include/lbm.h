@@ -1,0 +1,187 @@
+/*
+ * lbm.h - C ABI of the GB300 high-order lattice Boltzmann channel solver.
+ *
+ * One solver = one force-driven plane channel (Feuchter & Schleifenbaum,
+ * "High-order lattice Boltzmann models for wall-bounded flows at finite
+ * Knudsen numbers", Sect. V and VI): Nx nodes along the periodic stream
+ * direction x, Ny nodes between two diffuse Maxwell walls at rest, a
+ * constant body acceleration g along x.  Every time step runs on the GPU:
+ * pull streaming, the diffuse-wall flux balance, moments, the order-N Hermite
+ * equilibrium, the body-force term and the trapezoidal BGK relaxation, fused
+ * in one kernel (Eq. nm.3, nm.4, nm.8, nm.10, nm.14, nm.15).
+ *
+ * Units (Sect. II, V): lengths in l0 = channel width, velocities in
+ * c0 = sqrt(R theta0), times in l0/c0.  Node j sits at y = (j + 1/2) dx with
+ * dx = 1/Ny, half a spacing from each wall (Sect. V).  dt = dx / c, so one
+ * step moves population a by its integer velocity e_a.  tau = sqrt(2/pi) Kn
+ * (Eq. nm.13).
+ *
+ * Conventions for every call:
+ *  - Every function returns LBM_OK (0) or a negative LBM_E* code; nothing
+ *    throws across the ABI and no call traps the device.
+ *  - "host" buffers are caller-owned CPU memory, "device" buffers are
+ *    caller-owned GPU memory on the solver's device.
+ *  - Calls are asynchronous on the solver's CUDA stream, except those that
+ *    return host values (lbm_moments, lbm_mass_flow, lbm_slip_velocity,
+ *    lbm_run_to_steady, lbm_status, lbm_get_state, lbm_populations), which
+ *    synchronise that stream before returning.
+ *  - A solver is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,      /* invalid argument (sizes, Kn, weights, pointers)   */
+    LBM_EDEGREE = -2,     /* quadrature order too low for the Hermite order    */
+    LBM_ENOMEM = -3,      /* device allocation failed / workspace too small    */
+    LBM_ECUDA = -4,       /* a CUDA runtime call failed                        */
+    LBM_ENONFINITE = -5,  /* a non-finite or non-positive density appeared     */
+    LBM_ETIMEOUT = -6,    /* a bounded device wait gave up                     */
+    LBM_ENOTCONV = -7,    /* lbm_run_to_steady reached max_steps               */
+    LBM_ENOTSUP = -8      /* valid but not supported by this build             */
+};
+
+/* Storage precision of the populations.  LBM_FP64 computes in fp64;
+ * LBM_FP32 stores fbar - w_a (deviation from the rest state at rho0 = 1) in
+ * fp32 and computes in fp32; moments handed to the host and every reduction
+ * are fp64 in all precisions. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1 };
+
+/* A two-dimensional discrete velocity model (Sect. II.A): velocities
+ * xi_a = c e_a with integer e_a, weights w_a.  The set must be closed under
+ * e -> -e with equal weights (all DVMs of the paper are), sum w_a = 1 to
+ * 1e-12, V <= LBM_MAX_V.  Caller-owned; copied by lbm_create. */
+#define LBM_MAX_V 128
+typedef struct {
+    int D;               /* must be 2                                       */
+    int V;               /* number of velocities                            */
+    const int* e;        /* V*2 ints, row-major (e_x, e_y), y = wall normal */
+    const double* w;     /* V weights                                       */
+    double c;            /* lattice speed                                   */
+} lbm_dvm;
+
+typedef struct lbm_solver lbm_solver;   /* opaque */
+
+/* ---- DVM utilities (host only, no GPU needed) --------------------------- */
+
+/* Expand printed symmetry groups into velocities (Eq. wdach): each
+ * representative reps[g*D .. g*D+D-1] (D = 2 or 3) generates the orbit under
+ * all component permutations and sign flips; every member gets weight wg[g].
+ * vg[g], if not NULL, is the group size the caller expects (checked).
+ * Outputs up to cap velocities into e_out (V*D ints) and w_out.
+ * Errors: LBM_EINVAL on a size mismatch or cap too small. */
+int lbm_dvm_expand(int D, int G, const int* reps, const int* vg, const double* wg,
+                   int cap, int* e_out, double* w_out, int* V_out);
+
+/* (x, z) marginal of a 3D set e3 (V3*3 ints, (x, y, z)): weights of
+ * velocities sharing (e_x, e_z) are summed.  Exact for flows uniform along y,
+ * the paper's channel (Sect. VI).  Output order: sorted by (e_x, e_z). */
+int lbm_dvm_marginal_xz(int V3, const int* e3, const double* w3, int cap,
+                        int* e2_out, double* w2_out, int* V2_out);
+
+/* Quadrature order Q of a 2D DVM (Eq. orth): the largest degree up to 16 for
+ * which every moment sum_a w_a xi_ax^i xi_ay^j, i + j <= Q, equals the
+ * Gaussian moment (i-1)!!(j-1)!! (relative tolerance 1e-9). */
+int lbm_dvm_quadrature_order(const lbm_dvm* dvm, int* Q_out);
+
+/* ---- solver lifetime ---------------------------------------------------- */
+
+/* Device bytes lbm_create_in needs for this problem (both population
+ * lattices, fp64 moment fields, reduction scratch). */
+int lbm_workspace_bytes(const lbm_dvm* dvm, int Nx, int Ny, int precision,
+                        size_t* bytes);
+
+/* Create a solver that allocates its own device memory with cudaMalloc on the
+ * current device.
+ *   order: Hermite order N of the equilibrium, 2 <= N <= 4 and Q >= 2N - 1
+ *          (Sect. III: N = (Q-1)/2 is optimal, (Q+1)/2 still admissible);
+ *          otherwise LBM_EDEGREE.  Q must also be >= 5.
+ *   Nx >= 1 (periodic), Ny >= max |e_y| (walls), Kn > 0, force = g_x
+ *   (0 allowed: then lbm_mass_flow returns mdot = NaN).
+ *   precision: LBM_FP64 or LBM_FP32.
+ *   stream: a cudaStream_t, or NULL for the legacy default stream.
+ * The state is undefined until lbm_init. */
+int lbm_create(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn,
+               double force, int precision, void* stream, lbm_solver** out);
+
+/* As lbm_create, but uses caller-owned device memory `workspace` of `bytes`
+ * (>= lbm_workspace_bytes; 256-byte aligned) instead of allocating; the
+ * workspace must outlive the solver.  LBM_ENOMEM if bytes is too small. */
+int lbm_create_in(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn,
+                  double force, int precision, void* stream, void* workspace,
+                  size_t bytes, lbm_solver** out);
+
+/* Release the solver (and its memory, if lbm_create allocated it). */
+void lbm_destroy(lbm_solver* s);
+
+const char* lbm_strerror(int code);
+
+/* ---- state ------------------------------------------------------------- */
+
+/* Initial state fbar_a = rho(x, y) w_a (fluid at rest).  rho_host: Ny*Nx
+ * doubles, row-major [y][x], copied host->device; NULL means rho = 1.
+ * Resets the step counter and the status word. */
+int lbm_init(lbm_solver* s, const double* rho_host);
+
+/* As lbm_init with rho already in device memory (Ny*Nx doubles). */
+int lbm_init_device(lbm_solver* s, const double* rho_device);
+
+/* Advance nsteps >= 0 time steps (Eq. nm.8 + streaming + walls), one fused
+ * kernel launch per step on the solver's stream.  Asynchronous. */
+int lbm_step(lbm_solver* s, long nsteps);
+
+/* Step until max over nodes of |u_x(t) - u_x(t - dt)| < tol, tested every
+ * check_every (>= 2) steps, or until max_steps in total.  Returns LBM_OK when
+ * converged, LBM_ENOTCONV otherwise; *steps_done and *last_du (either may be
+ * NULL) report the total steps and the last tested change. */
+int lbm_run_to_steady(lbm_solver* s, double tol, long max_steps,
+                      long check_every, long* steps_done, double* last_du);
+
+/* Moments of the current state (Eq. nm.10): rho, u_x, u_y in units of rho0
+ * and c0, each Ny*Nx doubles [y][x] (host).  Any pointer may be NULL. */
+int lbm_moments(lbm_solver* s, double* rho, double* ux, double* uy);
+
+/* Normalised mass flow (Eq. pf.1) mdot = 2 tau <u_x> / (g Kn), <u_x> the
+ * mean over all nodes (midpoint rule).  Either pointer may be NULL. */
+int lbm_mass_flow(lbm_solver* s, double* mdot, double* mean_ux);
+
+/* Slip velocity u_s = u(wall)/u(centre) (Eq. defSlip).  u(wall): quadratic
+ * extrapolation (15 u_0 - 10 u_1 + 3 u_2)/8 from the three nodes nearest to
+ * each wall, averaged over both walls and all x; u(centre): the centre node
+ * for odd Ny, the four-point midpoint interpolation
+ * (9(u_{m-1} + u_m) - (u_{m-2} + u_{m+1}))/16, m = Ny/2, for even Ny.
+ * Needs Ny >= 4. */
+int lbm_slip_velocity(lbm_solver* s, double* us);
+
+/* Device status word: LBM_OK, or LBM_ENONFINITE once any step met a
+ * non-finite or non-positive density.  Synchronises the stream. */
+int lbm_status(lbm_solver* s);
+
+/* Steps taken since lbm_init. */
+int lbm_steps_done(lbm_solver* s, long* steps);
+
+/* Post-collision populations fbar*_a(x, y) of the last step (the state the
+ * next streaming step reads), as fp64, V*Ny*Nx doubles, planes in the
+ * caller's velocity order [a][y][x] (host). */
+int lbm_populations(lbm_solver* s, double* f_host);
+
+/* Checkpoint / resume: an opaque byte image of the state (populations in
+ * storage precision, moment fields, step counter).  lbm_state_bytes gives the
+ * size; restoring into a solver created with the same arguments continues
+ * bit-identically. */
+int lbm_state_bytes(lbm_solver* s, size_t* bytes);
+int lbm_get_state(lbm_solver* s, void* host, size_t bytes);
+int lbm_set_state(lbm_solver* s, const void* host, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,255 @@
+"""GB300-native high-order lattice Boltzmann solver for force-driven plane
+channels with diffuse Maxwell walls (Feuchter & Schleifenbaum, Sect. V, VI).
+
+Thin Python binding over the C ABI of include/lbm.h: every step of the
+solve runs in the library's CUDA kernels; PyTorch only provides device
+memory (the solver workspace) and the CUDA stream.
+
+    import paper_1510_08886_gb300 as lbm
+    e, w, c = lbm.dvm("D2V33")
+    s = lbm.Solver(e, w, c, order=4, Nx=4096, Ny=512, Kn=0.1,
+                   force=lbm.force_for_mach(0.1), precision="fp32")
+    s.init(); s.step(1000); print(s.mass_flow(), s.slip_velocity())
+"""
+import ctypes
+import math
+
+import numpy as np
+
+from . import _lib
+from ._lib import LBMError, check, lbm_dvm
+
+__all__ = ["dvm", "dvm_from_groups", "Solver", "LBMError", "force_for_mach", "tau_of_kn",
+           "quadrature_order"]
+
+PRECISIONS = {"fp64": _lib.LBM_FP64, "fp32": _lib.LBM_FP32}
+
+
+def tau_of_kn(Kn):
+    """tau = sqrt(2/pi) Kn (Eq. nm.13), in units of l0/c0."""
+    return math.sqrt(2.0 / math.pi) * Kn
+
+
+def force_for_mach(Kn, mach=1e-3):
+    """g such that the no-slip Navier-Stokes centre-line speed g/(8 nu),
+    nu = tau (Eq. nm.11, Sect. VI), equals ``mach`` (in units of c0)."""
+    return 8.0 * tau_of_kn(Kn) * mach
+
+
+def _ip(a):
+    return a.ctypes.data_as(_lib.c_int_p)
+
+
+def _dp(a):
+    return a.ctypes.data_as(_lib.c_double_p)
+
+
+def dvm_from_groups(table):
+    """Expand a printed group table (dict with D, c, groups) with the
+    library's lbm_dvm_expand.  Returns (e int32 (V, D), w float64 (V,), c)."""
+    D = int(table["D"])
+    reps = np.ascontiguousarray([list(g[0]) for g in table["groups"]], dtype=np.int32)
+    vg = np.ascontiguousarray([g[1] for g in table["groups"]], dtype=np.int32)
+    wg = np.ascontiguousarray([g[2] for g in table["groups"]], dtype=np.float64)
+    cap = int(vg.sum())
+    e = np.zeros((cap, D), dtype=np.int32)
+    w = np.zeros(cap)
+    V = ctypes.c_int(0)
+    check(_lib.lib().lbm_dvm_expand(D, len(wg), _ip(reps), _ip(vg), _dp(wg), cap, _ip(e),
+                                    _dp(w), ctypes.byref(V)), "lbm_dvm_expand")
+    return e[:V.value], w[:V.value], float(table["c"])
+
+
+def dvm(name, tables=None):
+    """Velocity set of a named DVM for the 2D channel: a 2D table of the
+    paper as printed, or '<3D name>xz' for the (x, z) marginal of a 3D table
+    (lbm_dvm_marginal_xz)."""
+    if tables is None:
+        from lbm_inputs import DVM_TABLES as tables
+    if name.endswith("xz"):
+        e3, w3, c = dvm_from_groups(tables[name[:-2]])
+        e3 = np.ascontiguousarray(e3, dtype=np.int32)
+        cap = len(w3)
+        e = np.zeros((cap, 2), dtype=np.int32)
+        w = np.zeros(cap)
+        V = ctypes.c_int(0)
+        check(_lib.lib().lbm_dvm_marginal_xz(len(w3), _ip(e3), _dp(np.ascontiguousarray(w3)),
+                                             cap, _ip(e), _dp(w), ctypes.byref(V)),
+              "lbm_dvm_marginal_xz")
+        return e[:V.value], w[:V.value], c
+    e, w, c = dvm_from_groups(tables[name])
+    if e.shape[1] != 2:
+        raise ValueError(f"{name} is three-dimensional; use '{name}xz'")
+    return e, w, c
+
+
+class _DVM:
+    """Keeps the arrays of an lbm_dvm alive."""
+
+    def __init__(self, e, w, c):
+        self.e = np.ascontiguousarray(np.asarray(e, dtype=np.int32).reshape(-1, 2))
+        self.w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+        self.s = lbm_dvm(2, len(self.w), _ip(self.e), _dp(self.w), float(c))
+
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def quadrature_order(e, w, c):
+    d = _DVM(e, w, c)
+    Q = ctypes.c_int(-1)
+    check(_lib.lib().lbm_dvm_quadrature_order(d.ref(), ctypes.byref(Q)))
+    return Q.value
+
+
+def _torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("paper_1510_08886_gb300.Solver needs a CUDA device "
+                           "(there is no CPU fallback)")
+    return torch
+
+
+class Solver:
+    """One channel solve on the GPU (see include/lbm.h for the semantics).
+
+    e (V, 2) integer velocities (x, y), y = wall normal; w (V,) weights;
+    c lattice speed; order = Hermite order N; Nx periodic nodes, Ny nodes
+    between the walls; Kn Knudsen number; force = g_x; precision 'fp64' or
+    'fp32'.  Device memory comes from a torch uint8 tensor (the workspace);
+    work is issued on ``stream`` (a torch.cuda.Stream) or torch's current
+    stream.
+    """
+
+    def __init__(self, e, w, c, order, Nx, Ny, Kn, force, precision="fp64", stream=None,
+                 device=None):
+        torch = _torch_cuda()
+        self._torch = torch
+        self.dvm = _DVM(e, w, c)
+        self.V = len(self.dvm.w)
+        self.order, self.Nx, self.Ny = int(order), int(Nx), int(Ny)
+        self.Kn, self.force, self.c = float(Kn), float(force), float(c)
+        self.precision = precision
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        prec = PRECISIONS[precision]
+        nbytes = ctypes.c_size_t(0)
+        L = _lib.lib()
+        check(L.lbm_workspace_bytes(self.dvm.ref(), self.Nx, self.Ny, prec, ctypes.byref(nbytes)),
+              "lbm_workspace_bytes")
+        self.workspace = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        h = ctypes.c_void_p()
+        check(L.lbm_create_in(self.dvm.ref(), self.order, self.Nx, self.Ny, self.Kn, self.force,
+                              prec, ctypes.c_void_p(self.stream.cuda_stream),
+                              ctypes.c_void_p(aligned), nbytes.value, ctypes.byref(h)),
+              "lbm_create_in")
+        self._h = h
+        self.tau = tau_of_kn(self.Kn)
+        self.dt = 1.0 / (self.Ny * self.c)
+
+    # lifetime ---------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def workspace_bytes(self):
+        return self.workspace.numel()
+
+    # stepping ---------------------------------------------------------------
+    def init(self, rho=None):
+        """fbar = rho w (fluid at rest).  rho: None (uniform 1), a host array
+        (Ny, Nx), or a CUDA float64 tensor of that shape."""
+        L = _lib.lib()
+        if rho is None:
+            check(L.lbm_init(self._h, None), "lbm_init")
+        elif hasattr(rho, "is_cuda") and rho.is_cuda:
+            r = rho.to(self._torch.float64).contiguous()
+            if r.numel() != self.Nx * self.Ny:
+                raise ValueError("rho has the wrong size")
+            self._rho_dev = r           # keep alive until the init kernel ran
+            check(L.lbm_init_device(self._h, ctypes.c_void_p(r.data_ptr())), "lbm_init_device")
+        else:
+            r = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(self.Ny, self.Nx))
+            check(L.lbm_init(self._h, _dp(r)), "lbm_init")
+        return self
+
+    def step(self, n=1):
+        check(_lib.lib().lbm_step(self._h, int(n)), "lbm_step")
+        return self
+
+    def run_to_steady(self, tol, max_steps, check_every=100):
+        """Returns (converged, steps_done, last_du)."""
+        steps = ctypes.c_long(0)
+        du = ctypes.c_double(0)
+        rc = _lib.lib().lbm_run_to_steady(self._h, float(tol), int(max_steps), int(check_every),
+                                          ctypes.byref(steps), ctypes.byref(du))
+        if rc not in (_lib.LBM_OK, _lib.LBM_ENOTCONV):
+            raise LBMError(rc, "lbm_run_to_steady")
+        return rc == _lib.LBM_OK, steps.value, du.value
+
+    # observables ------------------------------------------------------------
+    def moments(self):
+        rho = np.empty((self.Ny, self.Nx))
+        ux = np.empty_like(rho)
+        uy = np.empty_like(rho)
+        check(_lib.lib().lbm_moments(self._h, _dp(rho), _dp(ux), _dp(uy)), "lbm_moments")
+        return rho, ux, uy
+
+    def mass_flow(self):
+        m = ctypes.c_double(0)
+        check(_lib.lib().lbm_mass_flow(self._h, ctypes.byref(m), None), "lbm_mass_flow")
+        return m.value
+
+    def mean_ux(self):
+        u = ctypes.c_double(0)
+        check(_lib.lib().lbm_mass_flow(self._h, None, ctypes.byref(u)), "lbm_mass_flow")
+        return u.value
+
+    def slip_velocity(self):
+        u = ctypes.c_double(0)
+        check(_lib.lib().lbm_slip_velocity(self._h, ctypes.byref(u)), "lbm_slip_velocity")
+        return u.value
+
+    def status(self):
+        return _lib.lib().lbm_status(self._h)
+
+    @property
+    def steps(self):
+        n = ctypes.c_long(0)
+        check(_lib.lib().lbm_steps_done(self._h, ctypes.byref(n)))
+        return n.value
+
+    def populations(self):
+        """Post-collision fbar* of the last step, (V, Ny, Nx), caller order."""
+        f = np.empty((self.V, self.Ny, self.Nx))
+        check(_lib.lib().lbm_populations(self._h, _dp(f)), "lbm_populations")
+        return f
+
+    def get_state(self):
+        n = ctypes.c_size_t(0)
+        check(_lib.lib().lbm_state_bytes(self._h, ctypes.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        check(_lib.lib().lbm_get_state(self._h, buf.ctypes.data_as(ctypes.c_void_p), n.value),
+              "lbm_get_state")
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(_lib.lib().lbm_set_state(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes),
+              "lbm_set_state")
+        return self

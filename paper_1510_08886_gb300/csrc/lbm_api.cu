@@ -1,0 +1,603 @@
+// Host implementation of the C ABI declared in include/lbm.h: solver set-up
+// and validation, workspace layout, the time-step loop, the steady-state
+// driver, the fp64 reductions (mass flow, slip velocity, convergence test)
+// and checkpoint / resume.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using lbm::DevBufs;
+using lbm::KParams;
+
+struct lbm_solver {
+    int precision = LBM_FP64;
+    int N = 3, Nx = 1, Ny = 1, V = 0, R = 0, P = 0, maxey = 0;
+    double c = 1, Kn = 0, tau = 0, dt = 0, g = 0, den = 0;
+    cudaStream_t stream = nullptr;
+    bool owns = false;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t elem = 8;
+    DevBufs b{};
+    int cur = 0;
+    long steps = 0;
+    std::vector<int> perm;       // internal plane -> caller velocity index
+    std::vector<int> ex, ey;     // internal order
+    std::vector<double> w;
+    KParams<double> k64{};
+    KParams<float> k32{};
+};
+
+namespace {
+
+constexpr unsigned kStateMagic = 0x4c424d31u;   // "LBM1"
+
+struct StateHeader {
+    unsigned magic;
+    int precision, V, Nx, Ny, N;
+    long steps;
+};
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+size_t elem_bytes(int precision) { return precision == LBM_FP32 ? 4 : 8; }
+
+struct Layout {
+    size_t f0, f1, rho, ux, uy, prev, partial, results, status, total;
+};
+
+Layout layout(int V, size_t ncell, size_t elem) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t n) { size_t o = off; off = align256(off + n); return o; };
+    L.f0 = take(size_t(V) * ncell * elem);
+    L.f1 = take(size_t(V) * ncell * elem);
+    L.rho = take(ncell * 8);
+    L.ux = take(ncell * 8);
+    L.uy = take(ncell * 8);
+    L.prev = take(ncell * 8);
+    L.partial = take(2 * lbm::kReduceBlocks * 8);
+    L.results = take(8 * 8);
+    L.status = take(256);
+    L.total = off;
+    return L;
+}
+
+// Validate the DVM and put it into pair order: rest plane first (if any),
+// then one member of each +-e pair, then the negatives in the same order.
+int canonicalize(const lbm_dvm* d, std::vector<int>& ex, std::vector<int>& ey,
+                 std::vector<double>& w, std::vector<int>& perm, int& R, int& P) {
+    if (!d || d->D != 2 || d->V < 1 || d->V > LBM_MAX_V || !d->e || !d->w) return LBM_EINVAL;
+    if (!(d->c > 0) || !std::isfinite(d->c)) return LBM_EINVAL;
+    const int V = d->V;
+    double sw = 0;
+    for (int a = 0; a < V; ++a) {
+        if (!(d->w[a] > 0) || !std::isfinite(d->w[a])) return LBM_EINVAL;
+        sw += d->w[a];
+        for (int b = 0; b < a; ++b)
+            if (d->e[2 * a] == d->e[2 * b] && d->e[2 * a + 1] == d->e[2 * b + 1]) return LBM_EINVAL;
+    }
+    if (std::fabs(sw - 1.0) > 1e-12) return LBM_EINVAL;
+    std::vector<int> rest, pos, neg;
+    for (int a = 0; a < V; ++a) {
+        const int x = d->e[2 * a], y = d->e[2 * a + 1];
+        if (x == 0 && y == 0) { rest.push_back(a); continue; }
+        if (!(y > 0 || (y == 0 && x > 0))) continue;
+        int m = -1;
+        for (int b = 0; b < V; ++b)
+            if (d->e[2 * b] == -x && d->e[2 * b + 1] == -y) m = b;
+        if (m < 0) return LBM_EINVAL;
+        if (std::fabs(d->w[m] - d->w[a]) > 1e-13 * d->w[a]) return LBM_EINVAL;
+        pos.push_back(a);
+        neg.push_back(m);
+    }
+    if (rest.size() > 1 || rest.size() + 2 * pos.size() != size_t(V)) return LBM_EINVAL;
+    R = int(rest.size());
+    P = int(pos.size());
+    perm.clear();
+    for (int a : rest) perm.push_back(a);
+    for (int a : pos) perm.push_back(a);
+    for (int a : neg) perm.push_back(a);
+    ex.resize(V);
+    ey.resize(V);
+    w.resize(V);
+    for (int i = 0; i < V; ++i) {
+        ex[i] = d->e[2 * perm[i]];
+        ey[i] = d->e[2 * perm[i] + 1];
+        w[i] = d->w[perm[i]];
+    }
+    // a pair carries one weight: the two members agree to 1e-13 (checked)
+    for (int p = 0; p < P; ++p) {
+        const double m = 0.5 * (w[R + p] + w[R + P + p]);
+        w[R + p] = w[R + P + p] = m;
+    }
+    return LBM_OK;
+}
+
+template <typename C>
+void fill_params(const lbm_solver* s, KParams<C>& k) {
+    std::memset(&k, 0, sizeof(k));
+    k.Nx = s->Nx;
+    k.Ny = s->Ny;
+    k.ncell = s->Nx * s->Ny;
+    k.R = s->R;
+    k.P = s->P;
+    k.V = s->V;
+    k.maxey = s->maxey;
+    k.force = s->g != 0.0;
+    k.emit = 0;
+    k.plane = (long long)s->Nx * s->Ny;
+    const double omega = s->dt / (s->tau + 0.5 * s->dt);   // Eq. nm.8
+    for (int a = 0; a < s->V; ++a) {
+        k.ex[a] = s->ex[a];
+        k.ey[a] = s->ey[a];
+        k.sx[a] = ((s->ex[a] % s->Nx) + s->Nx) % s->Nx;
+        k.w[a] = s->w[a];
+    }
+    k.inv_den = 1.0 / s->den;
+    for (int p = 0; p < s->P; ++p) {
+        const int a = s->R + p;
+        const double x = s->ex[a], y = s->ey[a];
+        k.pex[p] = C(x);
+        k.pey[p] = C(y);
+        k.pexx[p] = C(x * x);
+        k.pexy2[p] = C(2 * x * y);
+        k.peyy[p] = C(y * y);
+        k.pge[p] = C(s->c * s->g * x);
+        k.pomw[p] = C(omega * s->w[a]);
+    }
+    k.omw_rest = C(s->R ? omega * s->w[0] : 0.0);
+    k.c = C(s->c);
+    k.c2 = C(s->c * s->c);
+    k.tau = C(s->tau);
+    k.dt = C(s->dt);
+    k.hdt = C(0.5 * s->dt);
+    k.omega = C(omega);
+    k.one_m_omega = C(1.0 - omega);
+    k.gx = C(s->g);
+    k.gy = C(0);
+    k.two_tau = C(2 * s->tau);
+    k.inv_2tau_dt = C(1.0 / (2 * s->tau + s->dt));
+    k.half_tau = C(0.5 * s->tau);
+}
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return LBM_OK;
+    return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+}
+
+__global__ void k_fill(double* p, int n, double v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// Partial sums for the fp64 reductions: per block, sum of u_x and
+// max |u_x - prev| (when prev is given).  Fixed shapes: deterministic.
+__global__ void __launch_bounds__(lbm::kReduceThreads)
+k_reduce_partial(const double* __restrict__ ux, const double* __restrict__ prev, int n,
+                 double* __restrict__ partial) {
+    __shared__ double ssum[lbm::kReduceThreads / 32], smax[lbm::kReduceThreads / 32];
+    double s = 0.0, m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double u = ux[i];
+        s += u;
+        if (prev) m = fmax(m, fabs(u - prev[i]));
+        if (u != u) m = u;   // propagate NaN into the convergence test
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        const double mo = __shfl_down_sync(0xffffffffu, m, o);
+        m = (mo != mo) ? mo : fmax(m, mo);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { ssum[wid] = s; smax[wid] = m; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ts = 0.0, tm = 0.0;
+        for (int k = 0; k < lbm::kReduceThreads / 32; ++k) {
+            ts += ssum[k];
+            tm = (smax[k] != smax[k]) ? smax[k] : fmax(tm, smax[k]);
+        }
+        partial[2 * blockIdx.x] = ts;
+        partial[2 * blockIdx.x + 1] = tm;
+    }
+}
+
+__device__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < int(blockDim.x >> 5); ++k) t += sh[k];
+    return t;   // valid in thread 0
+}
+
+// Final reduction (one block of 256): mean u_x, max |du|, slip velocity
+// (Eq. defSlip, quadratic wall extrapolation, centre interpolation) and the
+// normalised mass flow (Eq. pf.1).
+__global__ void __launch_bounds__(256)
+k_reduce_final(const double* __restrict__ partial, int nblk, const double* __restrict__ ux,
+               int Nx, int Ny, double tau, double g, double Kn, double* __restrict__ res) {
+    __shared__ double sh[32];
+    __shared__ double rows[10];
+    double s = 0.0, m = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        s += partial[2 * i];
+        const double mi = partial[2 * i + 1];
+        m = (mi != mi) ? mi : fmax(m, mi);
+    }
+    const double tot = block_sum(s, sh);
+    // max over threads
+    for (int o = 16; o > 0; o >>= 1) {
+        const double mo = __shfl_down_sync(0xffffffffu, m, o);
+        m = (mo != mo) ? mo : fmax(m, mo);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    double mx = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < int(blockDim.x >> 5); ++k) mx = (sh[k] != sh[k]) ? sh[k] : fmax(mx, sh[k]);
+    __syncthreads();
+    // row means of u_x for the slip velocity
+    const int m2 = Ny / 2;
+    int rlist[10] = {0, 1, 2, Ny - 1, Ny - 2, Ny - 3, m2 - 2, m2 - 1, m2, m2 + 1};
+    if (Ny & 1) rlist[6] = rlist[7] = rlist[8] = rlist[9] = (Ny - 1) / 2;
+    const bool slip_ok = Ny >= 4;
+    for (int r = 0; r < 10; ++r) {
+        double v = 0.0;
+        if (slip_ok)
+            for (int x = threadIdx.x; x < Nx; x += blockDim.x) v += ux[(long long)rlist[r] * Nx + x];
+        const double t = block_sum(v, sh);
+        if (threadIdx.x == 0) rows[r] = t / Nx;
+    }
+    if (threadIdx.x == 0) {
+        const double mean = tot / ((double)Nx * Ny);
+        res[0] = mean;
+        res[1] = mx;
+        double us = nan("");
+        if (slip_ok) {
+            const double bot = (15.0 * rows[0] - 10.0 * rows[1] + 3.0 * rows[2]) / 8.0;
+            const double top = (15.0 * rows[3] - 10.0 * rows[4] + 3.0 * rows[5]) / 8.0;
+            const double uc = (Ny & 1) ? rows[8]
+                                       : (9.0 * (rows[7] + rows[8]) - (rows[6] + rows[9])) / 16.0;
+            us = 0.5 * (bot + top) / uc;
+        }
+        res[2] = us;
+        res[3] = g != 0.0 ? 2.0 * tau * mean / (g * Kn) : nan("");
+    }
+}
+
+int launch_step(lbm_solver* s, bool emit) {
+    const void* src = static_cast<const char*>(s->b.f[s->cur]);
+    void* dst = s->b.f[1 - s->cur];
+    cudaError_t e;
+    if (s->precision == LBM_FP64) {
+        s->k64.emit = emit;
+        e = lbm::launch_step_fp64(s->k64, s->N, src, dst, s->b, s->stream);
+    } else {
+        s->k32.emit = emit;
+        e = lbm::launch_step_fp32(s->k32, s->N, src, dst, s->b, s->stream);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    s->cur = 1 - s->cur;
+    s->steps += 1;
+    return LBM_OK;
+}
+
+int launch_init(lbm_solver* s, const double* rho_dev) {
+    s->cur = 0;
+    s->steps = 0;
+    cudaError_t e = cudaMemsetAsync(s->b.status, 0, sizeof(unsigned), s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (s->precision == LBM_FP64) {
+        s->k64.emit = 1;
+        e = lbm::launch_init_fp64(s->k64, s->N, rho_dev, s->b.f[0], s->b, s->stream);
+    } else {
+        s->k32.emit = 1;
+        e = lbm::launch_init_fp32(s->k32, s->N, rho_dev, s->b.f[0], s->b, s->stream);
+    }
+    return cuda_status(e);
+}
+
+int reduce(lbm_solver* s, bool with_prev, double out[4]) {
+    const int n = s->Nx * s->Ny;
+    k_reduce_partial<<<lbm::kReduceBlocks, lbm::kReduceThreads, 0, s->stream>>>(
+        s->b.ux, with_prev ? s->b.prev_ux : nullptr, n, s->b.partial);
+    k_reduce_final<<<1, 256, 0, s->stream>>>(s->b.partial, lbm::kReduceBlocks, s->b.ux, s->Nx,
+                                             s->Ny, s->tau, s->g, s->Kn, s->b.results);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, s->b.results, 4 * sizeof(double),
+                                              cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return cuda_status(e);
+}
+
+int read_status(lbm_solver* s) {
+    unsigned st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, s->b.status, sizeof(st), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return st ? LBM_ENONFINITE : LBM_OK;
+}
+
+int create_common(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, double force,
+                  int precision, void* stream, void* workspace, size_t bytes, bool own,
+                  lbm_solver** out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if (precision != LBM_FP64 && precision != LBM_FP32) return LBM_EINVAL;
+    if (Nx < 1 || Ny < 1 || !(Kn > 0) || !std::isfinite(Kn) || !std::isfinite(force))
+        return LBM_EINVAL;
+    if ((long long)Nx * Ny > (long long)0x7fffffff) return LBM_EINVAL;
+    lbm_solver* s = new (std::nothrow) lbm_solver();
+    if (!s) return LBM_ENOMEM;
+    int rc = canonicalize(dvm, s->ex, s->ey, s->w, s->perm, s->R, s->P);
+    if (rc) { delete s; return rc; }
+    int Q = -1;
+    lbm_dvm_quadrature_order(dvm, &Q);
+    if (order < 2 || order > 4 || Q < 5 || Q < 2 * order - 1) { delete s; return LBM_EDEGREE; }
+    s->V = dvm->V;
+    s->maxey = 0;
+    for (int a = 0; a < s->V; ++a) s->maxey = std::max(s->maxey, std::abs(s->ey[a]));
+    if (Ny < s->maxey || s->maxey == 0) { delete s; return LBM_EINVAL; }
+    s->precision = precision;
+    s->N = order;
+    s->Nx = Nx;
+    s->Ny = Ny;
+    s->c = dvm->c;
+    s->Kn = Kn;
+    s->tau = std::sqrt(2.0 / M_PI) * Kn;    // Eq. nm.13
+    s->dt = (1.0 / Ny) / dvm->c;            // dx = l0 / Ny, one hop per step
+    s->g = force;
+    s->den = 0.0;
+    for (int a = 0; a < s->V; ++a)
+        if (s->ey[a] > 0) s->den += s->ey[a] * s->w[a];
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->elem = elem_bytes(precision);
+    const Layout L = layout(s->V, size_t(Nx) * Ny, s->elem);
+    if (own) {
+        cudaError_t e = cudaMalloc(&s->ws, L.total);
+        if (e != cudaSuccess) { delete s; return LBM_ENOMEM; }
+        s->owns = true;
+    } else {
+        if (!workspace || bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+            delete s;
+            return workspace && bytes < L.total ? LBM_ENOMEM : LBM_EINVAL;
+        }
+        s->ws = workspace;
+    }
+    s->ws_bytes = L.total;
+    char* base = static_cast<char*>(s->ws);
+    s->b.f[0] = base + L.f0;
+    s->b.f[1] = base + L.f1;
+    s->b.rho = reinterpret_cast<double*>(base + L.rho);
+    s->b.ux = reinterpret_cast<double*>(base + L.ux);
+    s->b.uy = reinterpret_cast<double*>(base + L.uy);
+    s->b.prev_ux = reinterpret_cast<double*>(base + L.prev);
+    s->b.partial = reinterpret_cast<double*>(base + L.partial);
+    s->b.results = reinterpret_cast<double*>(base + L.results);
+    s->b.status = reinterpret_cast<unsigned*>(base + L.status);
+    fill_params(s, s->k64);
+    fill_params(s, s->k32);
+    *out = s;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_strerror(int code) {
+    switch (code) {
+        case LBM_OK: return "ok";
+        case LBM_EINVAL: return "invalid argument";
+        case LBM_EDEGREE: return "quadrature order too low for the Hermite order";
+        case LBM_ENOMEM: return "out of device memory or workspace too small";
+        case LBM_ECUDA: return "CUDA runtime error";
+        case LBM_ENONFINITE: return "non-finite or non-positive density";
+        case LBM_ETIMEOUT: return "bounded device wait timed out";
+        case LBM_ENOTCONV: return "not converged within max_steps";
+        case LBM_ENOTSUP: return "not supported";
+        default: return "unknown error";
+    }
+}
+
+int lbm_workspace_bytes(const lbm_dvm* dvm, int Nx, int Ny, int precision, size_t* bytes) {
+    if (!dvm || !bytes || Nx < 1 || Ny < 1 || dvm->V < 1 || dvm->V > LBM_MAX_V) return LBM_EINVAL;
+    if (precision != LBM_FP64 && precision != LBM_FP32) return LBM_EINVAL;
+    *bytes = layout(dvm->V, size_t(Nx) * Ny, elem_bytes(precision)).total;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, double force,
+               int precision, void* stream, lbm_solver** out) {
+    return create_common(dvm, order, Nx, Ny, Kn, force, precision, stream, nullptr, 0, true, out);
+}
+
+int lbm_create_in(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, double force,
+                  int precision, void* stream, void* workspace, size_t bytes,
+                  lbm_solver** out) {
+    return create_common(dvm, order, Nx, Ny, Kn, force, precision, stream, workspace, bytes,
+                         false, out);
+}
+
+void lbm_destroy(lbm_solver* s) {
+    if (!s) return;
+    if (s->owns && s->ws) {
+        cudaStreamSynchronize(s->stream);
+        cudaFree(s->ws);
+    }
+    delete s;
+}
+
+int lbm_init(lbm_solver* s, const double* rho_host) {
+    if (!s) return LBM_EINVAL;
+    const int n = s->Nx * s->Ny;
+    cudaError_t e;
+    if (rho_host)
+        e = cudaMemcpyAsync(s->b.prev_ux, rho_host, size_t(n) * 8, cudaMemcpyHostToDevice, s->stream);
+    else {
+        k_fill<<<(n + 255) / 256, 256, 0, s->stream>>>(s->b.prev_ux, n, 1.0);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    return launch_init(s, s->b.prev_ux);
+}
+
+int lbm_init_device(lbm_solver* s, const double* rho_device) {
+    if (!s || !rho_device) return LBM_EINVAL;
+    return launch_init(s, rho_device);
+}
+
+int lbm_step(lbm_solver* s, long nsteps) {
+    if (!s || nsteps < 0) return LBM_EINVAL;
+    for (long i = 0; i < nsteps; ++i) {
+        const int rc = launch_step(s, i == nsteps - 1);
+        if (rc) return rc;
+    }
+    return LBM_OK;
+}
+
+int lbm_run_to_steady(lbm_solver* s, double tol, long max_steps, long check_every,
+                      long* steps_done, double* last_du) {
+    if (!s || !(tol > 0) || max_steps < 0 || check_every < 2) return LBM_EINVAL;
+    double du = HUGE_VAL;
+    int rc = LBM_ENOTCONV;
+    while (s->steps < max_steps) {
+        const long n = std::min(check_every, max_steps - s->steps);
+        if (n > 1 && (rc = lbm_step(s, n - 1))) break;
+        cudaError_t e = cudaMemcpyAsync(s->b.prev_ux, s->b.ux, size_t(s->Nx) * s->Ny * 8,
+                                        cudaMemcpyDeviceToDevice, s->stream);
+        if (e != cudaSuccess) { rc = cuda_status(e); break; }
+        if ((rc = lbm_step(s, 1))) break;
+        double r[4];
+        if ((rc = reduce(s, true, r))) break;
+        du = r[1];
+        if ((rc = read_status(s))) break;
+        rc = LBM_ENOTCONV;
+        if (du < tol) { rc = LBM_OK; break; }
+    }
+    if (steps_done) *steps_done = s->steps;
+    if (last_du) *last_du = du;
+    return rc;
+}
+
+int lbm_moments(lbm_solver* s, double* rho, double* ux, double* uy) {
+    if (!s) return LBM_EINVAL;
+    const size_t n = size_t(s->Nx) * s->Ny * 8;
+    cudaError_t e = cudaSuccess;
+    if (rho && e == cudaSuccess) e = cudaMemcpyAsync(rho, s->b.rho, n, cudaMemcpyDeviceToHost, s->stream);
+    if (ux && e == cudaSuccess) e = cudaMemcpyAsync(ux, s->b.ux, n, cudaMemcpyDeviceToHost, s->stream);
+    if (uy && e == cudaSuccess) e = cudaMemcpyAsync(uy, s->b.uy, n, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return read_status(s);
+}
+
+int lbm_mass_flow(lbm_solver* s, double* mdot, double* mean_ux) {
+    if (!s) return LBM_EINVAL;
+    double r[4];
+    int rc = reduce(s, false, r);
+    if (rc) return rc;
+    if (mdot) *mdot = r[3];
+    if (mean_ux) *mean_ux = r[0];
+    return read_status(s);
+}
+
+int lbm_slip_velocity(lbm_solver* s, double* us) {
+    if (!s || !us) return LBM_EINVAL;
+    if (s->Ny < 4) return LBM_EINVAL;
+    double r[4];
+    int rc = reduce(s, false, r);
+    if (rc) return rc;
+    *us = r[2];
+    return read_status(s);
+}
+
+int lbm_status(lbm_solver* s) {
+    if (!s) return LBM_EINVAL;
+    return read_status(s);
+}
+
+int lbm_steps_done(lbm_solver* s, long* steps) {
+    if (!s || !steps) return LBM_EINVAL;
+    *steps = s->steps;
+    return LBM_OK;
+}
+
+int lbm_populations(lbm_solver* s, double* f_host) {
+    if (!s || !f_host) return LBM_EINVAL;
+    const size_t n = size_t(s->Nx) * s->Ny;
+    std::vector<char> raw(size_t(s->V) * n * s->elem);
+    cudaError_t e = cudaMemcpyAsync(raw.data(), s->b.f[s->cur], raw.size(), cudaMemcpyDeviceToHost,
+                                    s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int a = 0; a < s->V; ++a) {
+        double* dst = f_host + size_t(s->perm[a]) * n;
+        for (size_t i = 0; i < n; ++i) {
+            const double d = s->precision == LBM_FP64
+                                 ? reinterpret_cast<const double*>(raw.data())[a * n + i]
+                                 : double(reinterpret_cast<const float*>(raw.data())[a * n + i]);
+            dst[i] = s->w[a] + d;
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_state_bytes(lbm_solver* s, size_t* bytes) {
+    if (!s || !bytes) return LBM_EINVAL;
+    const size_t n = size_t(s->Nx) * s->Ny;
+    *bytes = sizeof(StateHeader) + size_t(s->V) * n * s->elem + 3 * n * 8;
+    return LBM_OK;
+}
+
+int lbm_get_state(lbm_solver* s, void* host, size_t bytes) {
+    size_t need = 0;
+    if (!host || lbm_state_bytes(s, &need) || bytes < need) return LBM_EINVAL;
+    const size_t n = size_t(s->Nx) * s->Ny;
+    StateHeader h{kStateMagic, s->precision, s->V, s->Nx, s->Ny, s->N, s->steps};
+    std::memcpy(host, &h, sizeof(h));
+    char* p = static_cast<char*>(host) + sizeof(h);
+    const size_t fb = size_t(s->V) * n * s->elem;
+    cudaError_t e = cudaMemcpyAsync(p, s->b.f[s->cur], fb, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + fb, s->b.rho, n * 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + fb + n * 8, s->b.ux, n * 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p + fb + 2 * n * 8, s->b.uy, n * 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return cuda_status(e);
+}
+
+int lbm_set_state(lbm_solver* s, const void* host, size_t bytes) {
+    size_t need = 0;
+    if (!host || lbm_state_bytes(s, &need) || bytes < need) return LBM_EINVAL;
+    StateHeader h;
+    std::memcpy(&h, host, sizeof(h));
+    if (h.magic != kStateMagic || h.precision != s->precision || h.V != s->V || h.Nx != s->Nx ||
+        h.Ny != s->Ny || h.N != s->N || h.steps < 0)
+        return LBM_EINVAL;
+    const size_t n = size_t(s->Nx) * s->Ny;
+    const char* p = static_cast<const char*>(host) + sizeof(h);
+    const size_t fb = size_t(s->V) * n * s->elem;
+    s->cur = 0;
+    cudaError_t e = cudaMemcpyAsync(s->b.f[0], p, fb, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->b.rho, p + fb, n * 8, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->b.ux, p + fb + n * 8, n * 8, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->b.uy, p + fb + 2 * n * 8, n * 8, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->b.status, 0, sizeof(unsigned), s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    s->steps = h.steps;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// Internal declarations shared by the host API (lbm_api.cu) and the kernel
+// translation units (k_fp64.cu, k_fp32.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm.h"
+
+namespace lbm {
+
+constexpr int kMaxPairs = LBM_MAX_V / 2;
+constexpr int kBlock = 256;          // threads per block of the step kernels
+constexpr int kReduceBlocks = 304;   // 2 x 152 SMs for the partial sums
+constexpr int kReduceThreads = 256;
+
+// Per-solve constants, passed by value to every kernel (__grid_constant__).
+// Planes are in the solver's internal order: R rest planes (R = 0 or 1),
+// then the P "positive" members of the +-e pairs, then their P negatives in
+// the same order, so plane R + P + p holds -e of plane R + p.
+template <typename C>
+struct KParams {
+    int Nx, Ny, ncell;           // ncell = Nx * Ny
+    int R, P, V;
+    int maxey;                   // max |e_y|: rows within maxey of a wall
+    int force;                   // 1 if g != 0
+    int emit;                    // 1: write fp64 rho, u of this step
+    long long plane;             // elements per plane = ncell
+    int ex[LBM_MAX_V], ey[LBM_MAX_V];
+    int sx[LBM_MAX_V];           // e_x mod Nx, in [0, Nx)
+    double w[LBM_MAX_V];         // weights (fp64) for the wall fill
+    double inv_den;              // 1 / sum_{e_y > 0} e_y w  (= same for e_y < 0)
+    // per pair p, positive member e = (ex, ey):
+    C pex[kMaxPairs], pey[kMaxPairs];
+    C pexx[kMaxPairs], pexy2[kMaxPairs], peyy[kMaxPairs];   // ex^2, 2 ex ey, ey^2
+    C pge[kMaxPairs];            // c g.e
+    C pomw[kMaxPairs];           // omega w_p
+    C omw_rest;                  // omega w_rest
+    // scalars
+    C c, c2, tau, dt, hdt, omega, one_m_omega, gx, gy;
+    C two_tau, inv_2tau_dt, half_tau;
+};
+
+// Device buffers of one solver.
+struct DevBufs {
+    void* f[2];                  // population lattices (ping-pong)
+    double* rho;                 // fp64 moments of the latest state
+    double* ux;
+    double* uy;
+    double* prev_ux;             // u_x one step earlier (convergence test); init staging
+    double* partial;             // 2 * kReduceBlocks reduction scratch
+    double* results;             // 8 doubles: mean_ux, max_du, u_s, mdot, ...
+    unsigned int* status;        // bit 0: non-finite / non-positive density
+};
+
+// Kernel launchers, one set per precision (k_fp64.cu, k_fp32.cu).
+// Return cudaSuccess or the launch error.
+cudaError_t launch_step_fp64(const KParams<double>& k, int N, const void* src,
+                             void* dst, const DevBufs& b, cudaStream_t st);
+cudaError_t launch_init_fp64(const KParams<double>& k, int N, const double* rho0,
+                             void* dst, const DevBufs& b, cudaStream_t st);
+cudaError_t launch_step_fp32(const KParams<float>& k, int N, const void* src,
+                             void* dst, const DevBufs& b, cudaStream_t st);
+cudaError_t launch_init_fp32(const KParams<float>& k, int N, const double* rho0,
+                             void* dst, const DevBufs& b, cudaStream_t st);
+
+}  // namespace lbm
