@@ -8,6 +8,7 @@
 #include <new>
 #include <vector>
 
+#include "dvm_sets.h"
 #include "lbm.h"
 #include "lbm_internal.h"
 
@@ -16,7 +17,7 @@ using lbm::KParams;
 
 struct lbm_solver {
     int precision = LBM_FP64;
-    int N = 3, Nx = 1, Ny = 1, V = 0, R = 0, P = 0, maxey = 0;
+    int N = 3, Nx = 1, Ny = 1, V = 0, R = 0, P = 0, maxey = 0, maxex = 0, set_id = -1;
     double c = 1, Kn = 0, tau = 0, dt = 0, g = 0, den = 0;
     cudaStream_t stream = nullptr;
     bool owns = false;
@@ -68,10 +69,46 @@ Layout layout(int V, size_t ncell, size_t elem) {
     return L;
 }
 
+// Velocity sets with compiled kernels, in the kernel dispatch order.
+struct CompiledSet {
+    int R, P;
+    const int* ex;
+    const int* ey;
+};
+template <class SET>
+constexpr CompiledSet compiled() { return {SET::R, SET::P, SET::ex, SET::ey}; }
+const CompiledSet kSets[] = {compiled<lbm::SetD2V16>(), compiled<lbm::SetD2V32>(),
+                             compiled<lbm::SetD2V33>(), compiled<lbm::SetD2V53>(),
+                             compiled<lbm::SetD2V40>(), compiled<lbm::SetD2V48>()};
+
+// If the velocity set equals a compiled one, reorder the pairs into its order
+// and return its index; else -1.
+int match_compiled(const lbm_dvm* d, int R, std::vector<int>& pos, std::vector<int>& neg) {
+    for (int id = 0; id < int(sizeof(kSets) / sizeof(kSets[0])); ++id) {
+        const CompiledSet& cs = kSets[id];
+        if (cs.R != R || cs.P != int(pos.size())) continue;
+        std::vector<int> np, nn;
+        for (int i = 0; i < cs.P; ++i) {
+            for (size_t j = 0; j < pos.size(); ++j)
+                if (d->e[2 * pos[j]] == cs.ex[i] && d->e[2 * pos[j] + 1] == cs.ey[i]) {
+                    np.push_back(pos[j]);
+                    nn.push_back(neg[j]);
+                    break;
+                }
+        }
+        if (int(np.size()) == cs.P) {
+            pos.swap(np);
+            neg.swap(nn);
+            return id;
+        }
+    }
+    return -1;
+}
+
 // Validate the DVM and put it into pair order: rest plane first (if any),
 // then one member of each +-e pair, then the negatives in the same order.
 int canonicalize(const lbm_dvm* d, std::vector<int>& ex, std::vector<int>& ey,
-                 std::vector<double>& w, std::vector<int>& perm, int& R, int& P) {
+                 std::vector<double>& w, std::vector<int>& perm, int& R, int& P, int& set_id) {
     if (!d || d->D != 2 || d->V < 1 || d->V > LBM_MAX_V || !d->e || !d->w) return LBM_EINVAL;
     if (!(d->c > 0) || !std::isfinite(d->c)) return LBM_EINVAL;
     const int V = d->V;
@@ -99,6 +136,7 @@ int canonicalize(const lbm_dvm* d, std::vector<int>& ex, std::vector<int>& ey,
     if (rest.size() > 1 || rest.size() + 2 * pos.size() != size_t(V)) return LBM_EINVAL;
     R = int(rest.size());
     P = int(pos.size());
+    set_id = match_compiled(d, R, pos, neg);
     perm.clear();
     for (int a : rest) perm.push_back(a);
     for (int a : pos) perm.push_back(a);
@@ -129,6 +167,8 @@ void fill_params(const lbm_solver* s, KParams<C>& k) {
     k.P = s->P;
     k.V = s->V;
     k.maxey = s->maxey;
+    k.maxex = s->maxex;
+    k.set_id = s->set_id;
     k.force = s->g != 0.0;
     k.emit = 0;
     k.plane = (long long)s->Nx * s->Ny;
@@ -137,6 +177,7 @@ void fill_params(const lbm_solver* s, KParams<C>& k) {
         k.ex[a] = s->ex[a];
         k.ey[a] = s->ey[a];
         k.sx[a] = ((s->ex[a] % s->Nx) + s->Nx) % s->Nx;
+        k.off[a] = s->ey[a] * s->Nx + s->ex[a];
         k.w[a] = s->w[a];
     }
     k.inv_den = 1.0 / s->den;
@@ -276,9 +317,21 @@ k_reduce_final(const double* __restrict__ partial, int nblk, const double* __res
     }
 }
 
+template <typename C>
+void set_plane_pointers(const lbm_solver* s, KParams<C>& k, const void* src, void* dst) {
+    const ptrdiff_t plane = ptrdiff_t(s->Nx) * s->Ny;
+    const ptrdiff_t es = ptrdiff_t(s->elem);
+    for (int a = 0; a < s->V; ++a) {
+        k.srcf[a] = static_cast<const char*>(src) + (a * plane - k.off[a]) * es;
+        k.dstp[a] = static_cast<char*>(dst) + a * plane * es;
+    }
+}
+
 int launch_step(lbm_solver* s, bool emit) {
     const void* src = static_cast<const char*>(s->b.f[s->cur]);
     void* dst = s->b.f[1 - s->cur];
+    set_plane_pointers(s, s->k64, src, dst);
+    set_plane_pointers(s, s->k32, src, dst);
     cudaError_t e;
     if (s->precision == LBM_FP64) {
         s->k64.emit = emit;
@@ -340,14 +393,17 @@ int create_common(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, doub
     if ((long long)Nx * Ny > (long long)0x7fffffff) return LBM_EINVAL;
     lbm_solver* s = new (std::nothrow) lbm_solver();
     if (!s) return LBM_ENOMEM;
-    int rc = canonicalize(dvm, s->ex, s->ey, s->w, s->perm, s->R, s->P);
+    int rc = canonicalize(dvm, s->ex, s->ey, s->w, s->perm, s->R, s->P, s->set_id);
     if (rc) { delete s; return rc; }
     int Q = -1;
     lbm_dvm_quadrature_order(dvm, &Q);
     if (order < 2 || order > 4 || Q < 5 || Q < 2 * order - 1) { delete s; return LBM_EDEGREE; }
     s->V = dvm->V;
     s->maxey = 0;
-    for (int a = 0; a < s->V; ++a) s->maxey = std::max(s->maxey, std::abs(s->ey[a]));
+    for (int a = 0; a < s->V; ++a) {
+        s->maxey = std::max(s->maxey, std::abs(s->ey[a]));
+        s->maxex = std::max(s->maxex, std::abs(s->ex[a]));
+    }
     if (Ny < s->maxey || s->maxey == 0) { delete s; return LBM_EINVAL; }
     s->precision = precision;
     s->N = order;

@@ -10,7 +10,18 @@
 namespace lbm {
 
 constexpr int kMaxPairs = LBM_MAX_V / 2;
-constexpr int kBlock = 256;          // threads per block of the step kernels
+constexpr int kBlock = 128;          // threads per block of the step kernels
+
+// Resident blocks per SM requested from the compiler for a register-resident
+// kernel with V populations of `bytes` each: the populations plus ~30
+// registers of per-node state, rounded to the allocation granularity of 8.
+// More resident warps keep more loads in flight, which this HBM-bound step
+// needs; the budget leaves the compiler room to avoid spills.
+constexpr int min_blocks_for(int V, int bytes) {
+    const int regs = ((V * bytes / 4 + (bytes == 4 ? 30 : 60)) + 7) / 8 * 8;
+    const int blocks = 65536 / (regs * kBlock);
+    return blocks < 1 ? 1 : (blocks > 16 ? 16 : blocks);
+}
 constexpr int kReduceBlocks = 304;   // 2 x 152 SMs for the partial sums
 constexpr int kReduceThreads = 256;
 
@@ -23,11 +34,19 @@ struct KParams {
     int Nx, Ny, ncell;           // ncell = Nx * Ny
     int R, P, V;
     int maxey;                   // max |e_y|: rows within maxey of a wall
+    int maxex;                   // max |e_x|
+    int set_id;                  // compiled velocity set (dvm_sets.h), -1: generic
     int force;                   // 1 if g != 0
     int emit;                    // 1: write fp64 rho, u of this step
     long long plane;             // elements per plane = ncell
     int ex[LBM_MAX_V], ey[LBM_MAX_V];
     int sx[LBM_MAX_V];           // e_x mod Nx, in [0, Nx)
+    int off[LBM_MAX_V];          // e_y Nx + e_x: pull offset of an interior node
+    // per launch: plane base pointers of the source lattice shifted by the
+    // interior pull offset (srcf[a] = src + a plane - off[a]) and of the
+    // destination lattice (dstp[a] = dst + a plane)
+    const void* srcf[LBM_MAX_V];
+    void* dstp[LBM_MAX_V];
     double w[LBM_MAX_V];         // weights (fp64) for the wall fill
     double inv_den;              // 1 / sum_{e_y > 0} e_y w  (= same for e_y < 0)
     // per pair p, positive member e = (ex, ey):

@@ -21,6 +21,9 @@
 
 #include <math.h>
 
+#include <utility>
+
+#include "dvm_sets.h"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -65,6 +68,9 @@ struct CellCoef {
     C tr;                     // tau rho
     C qxx, qxy, qyy, qtr;     // (tau/2) Q = qxx ex^2 + qxy 2 ex ey + qyy ey^2 - qtr
     C hx, hy;                 // tau (g.A).xi = hx ex + hy ey
+    // compile-time-velocity path, g along x (g.xi = c g_x e_x):
+    C trcg;                   // tau rho c g_x:  even part += e_x trcg s
+    C k0, cqxx, cqxy, cqyy;   // odd part += e_x (k0 + cqxx ex^2 + cqxy 2 ex ey + cqyy ey^2)
 };
 
 template <int N, typename C>
@@ -116,6 +122,12 @@ __device__ __forceinline__ CellCoef<C> cell_coef(const KParams<C>& k, C drho, C 
         } else {
             q.qxx = q.qxy = q.qyy = q.qtr = q.hx = q.hy = C(0);
         }
+        const C cg = k.c * k.gx;
+        q.trcg = q.tr * cg;
+        q.k0 = cg * (q.tr - q.qtr);
+        q.cqxx = cg * q.qxx;
+        q.cqxy = cg * q.qxy;
+        q.cqyy = cg * q.qyy;
     }
     return q;
 }
@@ -165,24 +177,109 @@ __device__ __forceinline__ C pull(const KParams<C>& k, const S* __restrict__ src
     return C(src[(long long)a * k.plane + (long long)(y - k.ey[a]) * k.Nx + xs]);
 }
 
-// Fused step for a DVM with R rest planes and P pairs known at compile time:
-// the V populations stay in registers between the moment pass and the
-// relaxation pass.
-template <int R, int P, int N, typename S, typename C>
-__global__ void __launch_bounds__(kBlock)
-k_step(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __restrict__ dst,
-       const DevBufs b) {
-    constexpr int V = R + 2 * P;
-    const int cell = blockIdx.x * kBlock + threadIdx.x;
-    if (cell >= k.ncell) return;
-    const int y = cell / k.Nx;
-    const int x = cell - y * k.Nx;
+// ---- compile-time velocity sets ---------------------------------------------
+// With e known at compile time, products with e components 0 and +-1 vanish
+// or become additions (IEEE rules forbid the compiler from folding x * 0).
+
+template <int E, typename C>
+__device__ __forceinline__ C mulc(C v) {          // E v, E != 0
+    if constexpr (E == 1) return v;
+    else if constexpr (E == -1) return -v;
+    else return C(E) * v;
+}
+
+template <int E, typename C>
+__device__ __forceinline__ C fmac(C a, C v) {     // a + E v
+    if constexpr (E == 0) return a;
+    else if constexpr (E == 1) return a + v;
+    else if constexpr (E == -1) return a - v;
+    else return fma(C(E), v, a);
+}
+
+template <int EX, int EY, typename C>
+__device__ __forceinline__ C lin(C x, C y) {      // EX x + EY y, (EX, EY) != 0
+    if constexpr (EX == 0) return mulc<EY>(y);
+    else if constexpr (EY == 0) return mulc<EX>(x);
+    else return fmac<EY>(mulc<EX>(x), y);
+}
+
+template <int EX, int EY, typename C>
+__device__ __forceinline__ void moment_pair(C fp, C fm, C& drho, C& Jx, C& Jy, C& Kxx, C& Kxy,
+                                            C& Kyy) {
+    const C sum = fp + fm, dif = fp - fm;
+    drho += sum;
+    Jx = fmac<EX>(Jx, dif);
+    Jy = fmac<EY>(Jy, dif);
+    Kxx = fmac<EX * EX>(Kxx, sum);
+    Kxy = fmac<EX * EY>(Kxy, sum);
+    Kyy = fmac<EY * EY>(Kyy, sum);
+}
+
+// Relax the pair (+e, -e), e = (EX, EY) known at compile time; same
+// arithmetic as pair_update with the force along x.
+template <int EX, int EY, int N, bool FORCE, typename C>
+__device__ __forceinline__ void pair_update_ct(const CellCoef<C>& q, C omw, C omo, C& fp, C& fm) {
+    const C s = lin<EX, EY>(q.utx, q.uty);
+    const C t = s * s;
+    C Ge = N >= 4 ? fma(t, fma(t, q.a2, q.a1), q.a0) : fma(t, q.a1, q.a0);
+    C Go = N >= 3 ? s * fma(t, q.b1, q.b0) : s * q.b0;
+    if constexpr (FORCE) {
+        if constexpr (EX != 0) {
+            // even: tau rho (g.xi) s; odd: (g.xi)(tau rho + (tau/2) Q)
+            Ge = fma(mulc<EX>(q.trcg), s, Ge);
+            C inner = q.k0;
+            inner = fmac<EX * EX>(inner, q.cqxx);
+            inner = fmac<2 * EX * EY>(inner, q.cqxy);
+            inner = fmac<EY * EY>(inner, q.cqyy);
+            Go = fmac<EX>(Go, inner);
+        }
+        Go = Go - lin<EX, EY>(q.hx, q.hy);      // - tau (g.A).xi
+    }
+    const C X = omw * Ge, Y = omw * Go;
+    fp = fma(omo, fp, X + Y);
+    fm = fma(omo, fm, X - Y);
+}
+
+template <class SET, typename C, int... I>
+__device__ __forceinline__ void moments_ct(const C* f, C& drho, C& Jx, C& Jy, C& Kxx, C& Kxy,
+                                           C& Kyy, std::integer_sequence<int, I...>) {
+    (moment_pair<SET::ex[I], SET::ey[I], C>(f[SET::R + I], f[SET::R + SET::P + I], drho, Jx, Jy,
+                                            Kxx, Kxy, Kyy), ...);
+}
+
+template <class SET, int N, bool FORCE, typename C, int... I>
+__device__ __forceinline__ void relax_ct(const KParams<C>& k, const CellCoef<C>& q, C* f,
+                                         std::integer_sequence<int, I...>) {
+    (pair_update_ct<SET::ex[I], SET::ey[I], N, FORCE, C>(q, k.pomw[I], k.one_m_omega,
+                                                         f[SET::R + I], f[SET::R + SET::P + I]), ...);
+}
+
+// Fused step for a compiled velocity set: the V populations stay in registers
+// between the moment pass and the relaxation pass.
+//  - fast path (block-uniform): the block's nodes lie in one row at least
+//    max|e_y| rows from both walls and max|e_x| columns from both ends, so
+//    every pull is a fixed offset from the node: one address per population;
+//  - general path: periodic wrap in x and the diffuse-wall fill near walls.
+template <class SET, int N, typename S, typename C>
+__global__ void __launch_bounds__(kBlock, min_blocks_for(SET::R + 2 * SET::P, sizeof(C)))
+k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __restrict__ dst,
+          const DevBufs b) {
+    constexpr int R = SET::R, P = SET::P, V = R + 2 * P;
+    const int c0 = blockIdx.x * kBlock;
+    const int cell = c0 + threadIdx.x;
+    const int y0 = c0 / k.Nx;
+    const int x0 = c0 - y0 * k.Nx;
+    const bool fast = x0 >= k.maxex && x0 + kBlock - 1 + k.maxex < k.Nx && y0 >= k.maxey &&
+                      y0 < k.Ny - k.maxey;
     C f[V];
-    const bool nb = y < k.maxey, nt = y >= k.Ny - k.maxey;
-    if (!(nb || nt)) {
+    if (fast) {
 #pragma unroll
-        for (int a = 0; a < V; ++a) f[a] = pull<S, C>(k, src, a, x, y);
+        for (int a = 0; a < V; ++a) f[a] = C(static_cast<const S*>(k.srcf[a])[cell]);
     } else {
+        if (cell >= k.ncell) return;
+        const int y = cell / k.Nx;
+        const int x = cell - y * k.Nx;
+        const bool nb = y < k.maxey, nt = y >= k.Ny - k.maxey;
         const double pb = nb ? wall_dpsi<S, C>(k, src, x, true) : 0.0;
         const double pt = nt ? wall_dpsi<S, C>(k, src, x, false) : 0.0;
 #pragma unroll
@@ -196,29 +293,16 @@ k_step(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __res
                 f[a] = pull<S, C>(k, src, a, x, y);
         }
     }
-    // moments of the deviations
     C drho = R ? f[0] : C(0), Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const C sum = f[R + p] + f[R + P + p], dif = f[R + p] - f[R + P + p];
-        drho += sum;
-        Jx = fma(k.pex[p], dif, Jx);
-        Jy = fma(k.pey[p], dif, Jy);
-        Kxx = fma(k.pexx[p], sum, Kxx);
-        Kxy = fma(k.pexy2[p], sum, Kxy);
-        Kyy = fma(k.peyy[p], sum, Kyy);
-    }
-    const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, C(0.5) * Kxy, Kyy);
+    moments_ct<SET, C>(f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, P>{});
+    const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, Kxy, Kyy);
     if (R) f[0] = fma(k.one_m_omega, f[0], k.omw_rest * q.a0);
-    if (k.force) {
+    if (k.force)
+        relax_ct<SET, N, true, C>(k, q, f, std::make_integer_sequence<int, P>{});
+    else
+        relax_ct<SET, N, false, C>(k, q, f, std::make_integer_sequence<int, P>{});
 #pragma unroll
-        for (int p = 0; p < P; ++p) pair_update<true, C>(k, q, p, f[R + p], f[R + P + p]);
-    } else {
-#pragma unroll
-        for (int p = 0; p < P; ++p) pair_update<false, C>(k, q, p, f[R + p], f[R + P + p]);
-    }
-#pragma unroll
-    for (int a = 0; a < V; ++a) dst[(long long)a * k.plane + cell] = S(f[a]);
+    for (int a = 0; a < V; ++a) static_cast<S*>(k.dstp[a])[cell] = S(f[a]);
     emit_moments<C>(k, q, cell, b);
     flag_density<C>(q, b.status);
 }
@@ -281,28 +365,21 @@ k_generic(const __grid_constant__ KParams<C> k, const S* __restrict__ src,
 template <typename C>
 inline dim3 grid_for(const KParams<C>& k) { return dim3((k.ncell + kBlock - 1) / kBlock); }
 
-// Dispatch on (R, P) to a register-resident instantiation, else the generic
-// kernel.  Listed shapes: the paper's 2D sets and the (x, z) marginals of its
-// 3D sets (V = 16, 32, 33, 37, 40, 41, 48, 53).
+// Dispatch: a compiled velocity set (dvm_sets.h) gets its register-resident
+// kernel, any other DVM the generic kernel.
 template <int N, typename S, typename C>
 cudaError_t launch_step_n(const KParams<C>& k, const S* src, S* dst, const DevBufs& b,
                           cudaStream_t st) {
     const dim3 g = grid_for(k);
-#define LBM_SHAPE(RR, PP)                                                     \
-    if (k.R == RR && k.P == PP) {                                             \
-        k_step<RR, PP, N, S, C><<<g, kBlock, 0, st>>>(k, src, dst, b);        \
-        return cudaGetLastError();                                            \
+    switch (k.set_id) {
+        case 0: k_step_ct<SetD2V16, N, S, C><<<g, kBlock, 0, st>>>(k, src, dst, b); break;
+        case 1: k_step_ct<SetD2V32, N, S, C><<<g, kBlock, 0, st>>>(k, src, dst, b); break;
+        case 2: k_step_ct<SetD2V33, N, S, C><<<g, kBlock, 0, st>>>(k, src, dst, b); break;
+        case 3: k_step_ct<SetD2V53, N, S, C><<<g, kBlock, 0, st>>>(k, src, dst, b); break;
+        case 4: k_step_ct<SetD2V40, N, S, C><<<g, kBlock, 0, st>>>(k, src, dst, b); break;
+        case 5: k_step_ct<SetD2V48, N, S, C><<<g, kBlock, 0, st>>>(k, src, dst, b); break;
+        default: k_generic<N, false, S, C><<<g, kBlock, 0, st>>>(k, src, nullptr, dst, b);
     }
-    LBM_SHAPE(0, 8)    // 16
-    LBM_SHAPE(0, 16)   // 32
-    LBM_SHAPE(1, 16)   // 33
-    LBM_SHAPE(1, 18)   // 37
-    LBM_SHAPE(0, 20)   // 40
-    LBM_SHAPE(1, 20)   // 41
-    LBM_SHAPE(0, 24)   // 48
-    LBM_SHAPE(1, 26)   // 53
-#undef LBM_SHAPE
-    k_generic<N, false, S, C><<<g, kBlock, 0, st>>>(k, src, nullptr, dst, b);
     return cudaGetLastError();
 }
 

@@ -141,3 +141,16 @@ def test_solver_requires_cuda(L):
     e, w, c = lbm.dvm("D2V16")
     with pytest.raises(RuntimeError, match="CUDA"):
         lbm.Solver(e, w, c, 3, 1, 16, 0.1, 1e-3)
+
+
+def test_compiled_set_header_is_current():
+    """csrc/dvm_sets.h is generated from the paper's tables; it must match a
+    fresh generation, and each compiled set must be the velocity set the
+    library's own expansion produces."""
+    import paper_1510_08886_gb300 as lbm
+    from paper_1510_08886_gb300 import gen_dvm_sets as gen
+    assert open(gen.HEADER).read() == gen.render()
+    for ident, tname, marg in gen.SETS:
+        e, w, c = lbm.dvm(tname + ("xz" if marg else ""))
+        rest, pos = gen.pairs_of({tuple(v) for v in e.tolist()})
+        assert len(pos) * 2 + rest == len(e)

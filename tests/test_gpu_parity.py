@@ -76,6 +76,25 @@ def test_fp64_parity_after_steps(name, N, Nx, Ny):
     assert np.max(np.abs(fs_g - fs_o[idx])) < 1e-13
 
 
+@pytest.mark.parametrize("name,N", [("D2V33", 4), ("D2V16", 3), ("D2V32", 3), ("D3V107xz", 3)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_parity_interior_fast_path(name, N, precision):
+    """Nx = 1024: full 256-node blocks in interior rows take the fixed-offset
+    pull path, the blocks at x = 0 and x = Nx - 256 the wrapping path, wall
+    rows the wall path; all three must agree with the oracle."""
+    Nx, Ny, Kn = 1024, 30, 0.2
+    g = oracle.force_for_mach(Kn, 1e-2)
+    rho = rho_field(Nx, Ny, seed=21)
+    s, ref, e = _pair(name, N, Nx, Ny, Kn, g, rho, precision=precision)
+    s.step(12)
+    ref.step(12)
+    tol = 1e-12 if precision == "fp64" else 2e-5
+    assert _rel(s.moments()[1], ref.moments()[1]) < tol
+    if precision == "fp64":
+        idx = _match_planes(e, ref)
+        assert np.max(np.abs(s.populations() - ref.collide(ref.f)[idx])) < 1e-13
+
+
 @pytest.mark.parametrize("name,N", [("D2V16", 3), ("D2V33", 4), ("D3V107xz", 3)])
 def test_fp64_minimum_ny(name, N):
     """Ny = max |e_y|: every row is a wall row of both walls."""
