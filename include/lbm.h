@@ -181,6 +181,35 @@ int lbm_state_bytes(lbm_solver* s, size_t* bytes);
 int lbm_get_state(lbm_solver* s, void* host, size_t bytes);
 int lbm_set_state(lbm_solver* s, const void* host, size_t bytes);
 
+/* ---- observables without allocation ------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that may not allocate device memory at all: a host process whose device
+ * memory is entirely owned by another runtime's pool allocator, or a loop that
+ * must not call cudaMalloc because the allocation would synchronise the
+ * device.  It computes the same observables as lbm_mass_flow and
+ * lbm_slip_velocity, but from a velocity field the caller owns, and it
+ * allocates nothing.
+ *
+ *   ux_device:  Ny*Nx doubles, row-major [y][x], u_x in units of c0 (device)
+ *   Nx >= 1, Ny >= 4, Nx*Ny <= 16,777,216 (larger fields: LBM_EINVAL)
+ *   Kn > 0, force = g_x: as in lbm_create (tau = sqrt(2/pi) Kn)
+ *   out_device: 3 doubles (device), written {<u_x>, mdot, u_s}; mdot is NaN
+ *               when force == 0
+ *   stream:     a cudaStream_t or NULL; the call is asynchronous on it
+ *
+ * Its scratch is one fixed array of 4096 doubles (32 KiB) in the library's
+ * device memory; every GPU that loads the library holds it until the process
+ * exits.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress, with that device current): make that first call
+ * before any stream capture.  Every call on a device shares the array, and a
+ * call overwrites every entry it reads before reading it, so nothing carries
+ * over from the previous call; calls that overlap on the GPU (other streams,
+ * other threads) race on it and must be serialised by the caller.  No
+ * cudaMalloc, cudaFree or allocating library routine is called. */
+int lbm_observables_noalloc(const double* ux_device, int Nx, int Ny, double Kn,
+                            double force, double* out_device, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,9 @@ SIGNATURES = {
     "lbm_state_bytes": (ctypes.c_int, [ctypes.c_void_p, c_size_p]),
     "lbm_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "lbm_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "lbm_observables_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
 }
 
 _lib = None
