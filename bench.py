@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--lb-steps", type=int, default=1000)
-    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     p.add_argument("--kn", type=float, default=0.1)
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -267,13 +267,14 @@ def main():
     ms_max = float(ms_t.item())
     launches = args.steps * args.lb_steps
     value = ws * ncell * launches / (ms_max * 1e-3) / 1e9
-    elem = 4 if args.precision == "fp32" else 8
+    ELEM = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+    elem = ELEM[args.precision]
     bytes_per_launch = 2 * V * elem * ncell          # read + write every population once
     avg_launch_s = ms * 1e-3 / launches
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / avg_launch_s / 1e9
     traffic = ncu_traffic(args.precision)
-    if args.precision == "fp32":
+    if args.precision != "fp64":
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind}
     else:
@@ -321,11 +322,12 @@ def main():
     # ---- variants: both precisions, Kn in {0.01, 0.1, 1.0} -----------------
     variants = []
     if not args.no_variants:
-        for prec in ("fp64", "fp32"):
-            for Kn in (0.01, 0.1, 1.0):
+        for prec, kns in (("fp64", (0.01, 0.1, 1.0)), ("fp32", (0.01, 0.1, 1.0)),
+                          ("fp16", (0.1,)), ("bf16", (0.1,))):
+            for Kn in kns:
                 lb = 200
                 vms, _, vst, vm = timed_run(prec, Kn, lb, 1, 1)
-                el = 4 if prec == "fp32" else 8
+                el = ELEM[prec]
                 variants.append({
                     "precision": prec, "Kn": Kn, "lb_steps": lb,
                     "GLUPS": ncell * lb / (vms * 1e-3) / 1e9,
@@ -342,12 +344,15 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "f64",
+            "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f32 (f16 storage)",
+                      "bf16": "f32 (bf16 storage)"}[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "Kn": args.kn, "lb_steps_per_step": args.lb_steps,
                        "cells": ncell, "velocities": V,
-                       "storage": ("fp32 deviations fbar - w" if args.precision == "fp32"
-                                   else "fp64 deviations fbar - w"),
+                       "storage": {"fp32": "fp32 deviations fbar - w",
+                                   "fp64": "fp64 deviations fbar - w",
+                                   "fp16": "fp16 (fbar - w)/(w S)",
+                                   "bf16": "bf16 (fbar - w)/(w S)"}[args.precision],
                        "l2": "inputs larger than L2 (two lattices of "
                              f"{V * elem * ncell / 1e6:.0f} MB each)",
                        "parallelism": f"replicas x{ws}"},

@@ -49,11 +49,16 @@ enum {
     LBM_ENOTSUP = -8      /* valid but not supported by this build             */
 };
 
-/* Storage precision of the populations.  LBM_FP64 computes in fp64;
- * LBM_FP32 stores fbar - w_a (deviation from the rest state at rho0 = 1) in
- * fp32 and computes in fp32; moments handed to the host and every reduction
+/* Storage precision of the populations.  Every precision stores the
+ * deviation d_a = fbar_a - w_a from the rest state at rho0 = 1.
+ *   LBM_FP64: d in fp64, fp64 arithmetic;
+ *   LBM_FP32: d in fp32, fp32 arithmetic;
+ *   LBM_FP16, LBM_BF16: h_a = d_a / (w_a S) in IEEE half / bfloat16, fp32
+ *     arithmetic; S is a per-solve power of 2 (initially 2^-6) that
+ *     lbm_run_to_steady refreshes at every test so that max |h| is in (1/2, 1].
+ * The wall flux balance, the moments handed to the host and every reduction
  * are fp64 in all precisions. */
-enum { LBM_FP64 = 0, LBM_FP32 = 1 };
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_BF16 = 3 };
 
 /* A two-dimensional discrete velocity model (Sect. II.A): velocities
  * xi_a = c e_a with integer e_a, weights w_a.  The set must be closed under
@@ -106,7 +111,7 @@ int lbm_workspace_bytes(const lbm_dvm* dvm, int Nx, int Ny, int precision,
  *          otherwise LBM_EDEGREE.  Q must also be >= 5.
  *   Nx >= 1 (periodic), Ny >= max |e_y| (walls), Kn > 0, force = g_x
  *   (0 allowed: then lbm_mass_flow returns mdot = NaN).
- *   precision: LBM_FP64 or LBM_FP32.
+ *   precision: LBM_FP64, LBM_FP32, LBM_FP16 or LBM_BF16.
  *   stream: a cudaStream_t, or NULL for the legacy default stream.
  * The state is undefined until lbm_init. */
 int lbm_create(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn,

@@ -22,7 +22,8 @@ from ._lib import LBMError, check, lbm_dvm
 __all__ = ["dvm", "dvm_from_groups", "Solver", "LBMError", "force_for_mach", "tau_of_kn",
            "quadrature_order"]
 
-PRECISIONS = {"fp64": _lib.LBM_FP64, "fp32": _lib.LBM_FP32}
+PRECISIONS = {"fp64": _lib.LBM_FP64, "fp32": _lib.LBM_FP32, "fp16": _lib.LBM_FP16,
+              "bf16": _lib.LBM_BF16}
 
 
 def tau_of_kn(Kn):
@@ -115,8 +116,8 @@ class Solver:
 
     e (V, 2) integer velocities (x, y), y = wall normal; w (V,) weights;
     c lattice speed; order = Hermite order N; Nx periodic nodes, Ny nodes
-    between the walls; Kn Knudsen number; force = g_x; precision 'fp64' or
-    'fp32'.  Device memory comes from a torch uint8 tensor (the workspace);
+    between the walls; Kn Knudsen number; force = g_x; precision 'fp64',
+    'fp32', 'fp16' or 'bf16'.  Device memory comes from a torch uint8 tensor (the workspace);
     work is issued on ``stream`` (a torch.cuda.Stream) or torch's current
     stream.
     """

@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liblbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_EDEGREE, LBM_ENOMEM, LBM_ECUDA = 0, -1, -2, -3, -4
 LBM_ENONFINITE, LBM_ETIMEOUT, LBM_ENOTCONV, LBM_ENOTSUP = -5, -6, -7, -8
-LBM_FP64, LBM_FP32 = 0, 1
+LBM_FP64, LBM_FP32, LBM_FP16, LBM_BF16 = 0, 1, 2, 3
 LBM_MAX_V = 128
 
 c_int_p = ctypes.POINTER(ctypes.c_int)

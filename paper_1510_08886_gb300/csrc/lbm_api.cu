@@ -2,6 +2,9 @@
 // and validation, workspace layout, the time-step loop, the steady-state
 // driver, the fp64 reductions (mass flow, slip velocity, convergence test)
 // and checkpoint / resume.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -19,6 +22,7 @@ struct lbm_solver {
     int precision = LBM_FP64;
     int N = 3, Nx = 1, Ny = 1, V = 0, R = 0, P = 0, maxey = 0, maxex = 0, set_id = -1;
     double c = 1, Kn = 0, tau = 0, dt = 0, g = 0, den = 0;
+    double scale = 1.0 / 64.0;   // S of the 16-bit storage (power of 2)
     cudaStream_t stream = nullptr;
     bool owns = false;
     void* ws = nullptr;
@@ -42,11 +46,17 @@ struct StateHeader {
     unsigned magic;
     int precision, V, Nx, Ny, N;
     long steps;
+    double scale;
 };
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
-size_t elem_bytes(int precision) { return precision == LBM_FP32 ? 4 : 8; }
+size_t elem_bytes(int precision) {
+    return precision == LBM_FP64 ? 8 : precision == LBM_FP32 ? 4 : 2;
+}
+
+bool valid_precision(int p) { return p >= LBM_FP64 && p <= LBM_BF16; }
+bool is16(int p) { return p == LBM_FP16 || p == LBM_BF16; }
 
 struct Layout {
     size_t f0, f1, rho, ux, uy, prev, partial, results, status, total;
@@ -179,6 +189,8 @@ void fill_params(const lbm_solver* s, KParams<C>& k) {
         k.sx[a] = ((s->ex[a] % s->Nx) + s->Nx) % s->Nx;
         k.off[a] = s->ey[a] * s->Nx + s->ex[a];
         k.w[a] = s->w[a];
+        k.sw[a] = C(s->w[a] * s->scale);
+        k.isw[a] = C(1.0 / (s->w[a] * s->scale));
     }
     k.inv_den = 1.0 / s->den;
     for (int p = 0; p < s->P; ++p) {
@@ -336,9 +348,14 @@ int launch_step(lbm_solver* s, bool emit) {
     if (s->precision == LBM_FP64) {
         s->k64.emit = emit;
         e = lbm::launch_step_fp64(s->k64, s->N, src, dst, s->b, s->stream);
-    } else {
+    } else if (s->precision == LBM_FP32) {
         s->k32.emit = emit;
         e = lbm::launch_step_fp32(s->k32, s->N, src, dst, s->b, s->stream);
+    } else {
+        s->k32.emit = emit;
+        s->k32.seed = unsigned(s->steps + 1);
+        e = lbm::launch_step_fp16(s->k32, s->N, s->precision == LBM_BF16, src, dst, s->b,
+                                  s->stream);
     }
     if (e != cudaSuccess) return cuda_status(e);
     s->cur = 1 - s->cur;
@@ -351,12 +368,21 @@ int launch_init(lbm_solver* s, const double* rho_dev) {
     s->steps = 0;
     cudaError_t e = cudaMemsetAsync(s->b.status, 0, sizeof(unsigned), s->stream);
     if (e != cudaSuccess) return cuda_status(e);
+    if (is16(s->precision) && s->scale != 1.0 / 64.0) {
+        s->scale = 1.0 / 64.0;
+        fill_params(s, s->k32);
+    }
     if (s->precision == LBM_FP64) {
         s->k64.emit = 1;
         e = lbm::launch_init_fp64(s->k64, s->N, rho_dev, s->b.f[0], s->b, s->stream);
-    } else {
+    } else if (s->precision == LBM_FP32) {
         s->k32.emit = 1;
         e = lbm::launch_init_fp32(s->k32, s->N, rho_dev, s->b.f[0], s->b, s->stream);
+    } else {
+        s->k32.emit = 1;
+        s->k32.seed = 0u;
+        e = lbm::launch_init_fp16(s->k32, s->N, s->precision == LBM_BF16, rho_dev, s->b.f[0],
+                                  s->b, s->stream);
     }
     return cuda_status(e);
 }
@@ -382,12 +408,35 @@ int read_status(lbm_solver* s) {
     return st ? LBM_ENONFINITE : LBM_OK;
 }
 
+// 16-bit storage: make max |h| over the state lie in (1/2, 1] by a power-of-2
+// change of S (exact up to the format's subnormal range).  Synchronises.
+int refresh_scale(lbm_solver* s) {
+    if (!is16(s->precision)) return LBM_OK;
+    const long long n = (long long)s->V * s->Nx * s->Ny;
+    float* out = reinterpret_cast<float*>(s->b.results + 6);
+    const bool bf = s->precision == LBM_BF16;
+    cudaError_t e = lbm::launch_absmax_fp16(s->b.f[s->cur], n, bf, out, s->stream);
+    float m = 0.f;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&m, out, sizeof(m), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!(m > 0.f) || !std::isfinite(m)) return LBM_OK;
+    const double target = std::ldexp(1.0, int(std::ceil(std::log2(double(m) * s->scale))));
+    const double ns = std::max(target, std::ldexp(1.0, -40));
+    if (ns == s->scale) return LBM_OK;
+    e = lbm::launch_rescale_fp16(s->b.f[s->cur], n, bf, float(s->scale / ns), s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    s->scale = ns;
+    fill_params(s, s->k32);
+    return LBM_OK;
+}
+
 int create_common(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, double force,
                   int precision, void* stream, void* workspace, size_t bytes, bool own,
                   lbm_solver** out) {
     if (!out) return LBM_EINVAL;
     *out = nullptr;
-    if (precision != LBM_FP64 && precision != LBM_FP32) return LBM_EINVAL;
+    if (!valid_precision(precision)) return LBM_EINVAL;
     if (Nx < 1 || Ny < 1 || !(Kn > 0) || !std::isfinite(Kn) || !std::isfinite(force))
         return LBM_EINVAL;
     if ((long long)Nx * Ny > (long long)0x7fffffff) return LBM_EINVAL;
@@ -469,7 +518,7 @@ const char* lbm_strerror(int code) {
 
 int lbm_workspace_bytes(const lbm_dvm* dvm, int Nx, int Ny, int precision, size_t* bytes) {
     if (!dvm || !bytes || Nx < 1 || Ny < 1 || dvm->V < 1 || dvm->V > LBM_MAX_V) return LBM_EINVAL;
-    if (precision != LBM_FP64 && precision != LBM_FP32) return LBM_EINVAL;
+    if (!valid_precision(precision)) return LBM_EINVAL;
     *bytes = layout(dvm->V, size_t(Nx) * Ny, elem_bytes(precision)).total;
     return LBM_OK;
 }
@@ -539,6 +588,7 @@ int lbm_run_to_steady(lbm_solver* s, double tol, long max_steps, long check_ever
         if ((rc = reduce(s, true, r))) break;
         du = r[1];
         if ((rc = read_status(s))) break;
+        if ((rc = refresh_scale(s))) break;
         rc = LBM_ENOTCONV;
         if (du < tol) { rc = LBM_OK; break; }
     }
@@ -601,9 +651,18 @@ int lbm_populations(lbm_solver* s, double* f_host) {
     for (int a = 0; a < s->V; ++a) {
         double* dst = f_host + size_t(s->perm[a]) * n;
         for (size_t i = 0; i < n; ++i) {
-            const double d = s->precision == LBM_FP64
-                                 ? reinterpret_cast<const double*>(raw.data())[a * n + i]
-                                 : double(reinterpret_cast<const float*>(raw.data())[a * n + i]);
+            double d;
+            if (s->precision == LBM_FP64)
+                d = reinterpret_cast<const double*>(raw.data())[a * n + i];
+            else if (s->precision == LBM_FP32)
+                d = double(reinterpret_cast<const float*>(raw.data())[a * n + i]);
+            else if (s->precision == LBM_FP16)
+                d = double(__half2float(reinterpret_cast<const __half*>(raw.data())[a * n + i])) *
+                    double(s->k32.sw[a]);
+            else
+                d = double(__bfloat162float(
+                        reinterpret_cast<const __nv_bfloat16*>(raw.data())[a * n + i])) *
+                    double(s->k32.sw[a]);
             dst[i] = s->w[a] + d;
         }
     }
@@ -621,7 +680,7 @@ int lbm_get_state(lbm_solver* s, void* host, size_t bytes) {
     size_t need = 0;
     if (!host || lbm_state_bytes(s, &need) || bytes < need) return LBM_EINVAL;
     const size_t n = size_t(s->Nx) * s->Ny;
-    StateHeader h{kStateMagic, s->precision, s->V, s->Nx, s->Ny, s->N, s->steps};
+    StateHeader h{kStateMagic, s->precision, s->V, s->Nx, s->Ny, s->N, s->steps, s->scale};
     std::memcpy(host, &h, sizeof(h));
     char* p = static_cast<char*>(host) + sizeof(h);
     const size_t fb = size_t(s->V) * n * s->elem;
@@ -653,6 +712,10 @@ int lbm_set_state(lbm_solver* s, const void* host, size_t bytes) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_status(e);
     s->steps = h.steps;
+    if (is16(s->precision)) {
+        s->scale = h.scale;
+        fill_params(s, s->k32);
+    }
     return LBM_OK;
 }
 

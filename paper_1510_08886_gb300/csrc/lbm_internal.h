@@ -38,6 +38,7 @@ struct KParams {
     int set_id;                  // compiled velocity set (dvm_sets.h), -1: generic
     int force;                   // 1 if g != 0
     int emit;                    // 1: write fp64 rho, u of this step
+    unsigned int seed;           // step counter: stochastic rounding of 16-bit stores
     long long plane;             // elements per plane = ncell
     int ex[LBM_MAX_V], ey[LBM_MAX_V];
     int sx[LBM_MAX_V];           // e_x mod Nx, in [0, Nx)
@@ -48,6 +49,9 @@ struct KParams {
     const void* srcf[LBM_MAX_V];
     void* dstp[LBM_MAX_V];
     double w[LBM_MAX_V];         // weights (fp64) for the wall fill
+    // 16-bit storage only: stored h_a = d_a / (w_a S), S a per-solve power of 2
+    C sw[LBM_MAX_V];             // w_a S      (load:  d = h * sw)
+    C isw[LBM_MAX_V];            // 1/(w_a S)  (store: h = d * isw)
     double inv_den;              // 1 / sum_{e_y > 0} e_y w  (= same for e_y < 0)
     // per pair p, positive member e = (ex, ey):
     C pex[kMaxPairs], pey[kMaxPairs];
@@ -82,5 +86,16 @@ cudaError_t launch_step_fp32(const KParams<float>& k, int N, const void* src,
                              void* dst, const DevBufs& b, cudaStream_t st);
 cudaError_t launch_init_fp32(const KParams<float>& k, int N, const double* rho0,
                              void* dst, const DevBufs& b, cudaStream_t st);
+// 16-bit storage (fp32 arithmetic): bf16 = false -> IEEE half, true -> bfloat16
+cudaError_t launch_step_fp16(const KParams<float>& k, int N, bool bf16, const void* src,
+                             void* dst, const DevBufs& b, cudaStream_t st);
+cudaError_t launch_init_fp16(const KParams<float>& k, int N, bool bf16, const double* rho0,
+                             void* dst, const DevBufs& b, cudaStream_t st);
+// max over the stored state of |h| (16-bit storage), into *out (device)
+cudaError_t launch_absmax_fp16(const void* f, long long n, bool bf16, float* out,
+                               cudaStream_t st);
+// multiply every stored value by `factor` (a power of 2)
+cudaError_t launch_rescale_fp16(void* f, long long n, bool bf16, float factor,
+                                cudaStream_t st);
 
 }  // namespace lbm

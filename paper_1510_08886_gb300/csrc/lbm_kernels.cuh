@@ -19,6 +19,8 @@
 // parts even and odd in e, each evaluated once per pair.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include <utility>
@@ -31,6 +33,70 @@ namespace lbm {
 template <typename C> __device__ __forceinline__ C cinf();
 template <> __device__ __forceinline__ double cinf<double>() { return HUGE_VAL; }
 template <> __device__ __forceinline__ float cinf<float>() { return HUGE_VALF; }
+
+// Storage of a population: fp64/fp32 hold the deviation d itself; the 16-bit
+// formats hold h = d / (w_a S) so that every plane uses the format's range
+// around 1 whatever its weight (d of a plane with w ~ 1e-6 would be subnormal).
+//
+// 16-bit stores round stochastically: with round-to-nearest the per-step
+// relaxation increment of a population is often below half an ulp of h and
+// is lost every step, which stalls the flow at a wrong state (2-6 % error in
+// the mass flow in fp16).  Adding uniform random bits below the kept mantissa
+// and truncating makes every store unbiased.  The random bits are a hash of
+// (node, step) advanced by a 32-bit LCG per plane (high bits only), so runs
+// are reproducible and a restored checkpoint continues bit for bit.
+template <typename S> struct Storage {
+    static constexpr bool scaled = false;
+};
+template <> struct Storage<__half> {
+    static constexpr bool scaled = true;
+    static __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half from_f(float v) { return __float2half_rn(v); }
+    // fp32 keeps 13 more mantissa bits than fp16
+    static __device__ __forceinline__ __half from_f_sr(float v, unsigned r) {
+        return __float2half_rz(__uint_as_float(__float_as_uint(v) + (r >> 19)));
+    }
+};
+template <> struct Storage<__nv_bfloat16> {
+    static constexpr bool scaled = true;
+    static __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 from_f(float v) { return __float2bfloat16_rn(v); }
+    // bf16 is the upper half of fp32
+    static __device__ __forceinline__ __nv_bfloat16 from_f_sr(float v, unsigned r) {
+        return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r >> 16)) >> 16));
+    }
+};
+
+__device__ __forceinline__ unsigned mix32(unsigned x) {   // integer hash (xorshift-multiply)
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ unsigned sr_seed(const KParams<C>& k, int cell) {
+    if constexpr (Storage<S>::scaled) return mix32(unsigned(cell) ^ mix32(k.seed * 0x9e3779b9u + 1u));
+    else return 0u;
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ C ld_pop(const KParams<C>& k, S v, int a) {
+    if constexpr (Storage<S>::scaled) return Storage<S>::to_f(v) * k.sw[a];
+    else return C(v);
+}
+
+template <typename S, typename C>
+__device__ __forceinline__ S st_pop(const KParams<C>& k, C v, int a, unsigned& r) {
+    if constexpr (Storage<S>::scaled) {
+        r = r * 1664525u + 1013904223u;
+        return Storage<S>::from_f_sr(v * k.isw[a], r);
+    } else {
+        return S(v);
+    }
+}
 
 // Wall flux balance (Eq. nm.15) for landing column x, in deviation form:
 // returns dPsi = sum_out d_b / sum_in |e_y| w  so that an unknown incoming
@@ -51,7 +117,7 @@ __device__ __noinline__ double wall_dpsi(const KParams<C>& k, const S* __restric
         const S* pl = src + (long long)b * k.plane + xs;
         for (int j = 0; j < n; ++j) {
             const int row = bottom ? j : (k.Ny - 1 - j);
-            acc += (double)pl[(long long)row * k.Nx];
+            acc += (double)ld_pop<S, C>(k, pl[(long long)row * k.Nx], b);
         }
     }
     return acc * k.inv_den;
@@ -174,7 +240,7 @@ template <typename S, typename C>
 __device__ __forceinline__ C pull(const KParams<C>& k, const S* __restrict__ src, int a, int x, int y) {
     int xs = x - k.sx[a];
     xs += (xs < 0) ? k.Nx : 0;
-    return C(src[(long long)a * k.plane + (long long)(y - k.ey[a]) * k.Nx + xs]);
+    return ld_pop<S, C>(k, src[(long long)a * k.plane + (long long)(y - k.ey[a]) * k.Nx + xs], a);
 }
 
 // ---- compile-time velocity sets ---------------------------------------------
@@ -274,7 +340,7 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
     C f[V];
     if (fast) {
 #pragma unroll
-        for (int a = 0; a < V; ++a) f[a] = C(static_cast<const S*>(k.srcf[a])[cell]);
+        for (int a = 0; a < V; ++a) f[a] = ld_pop<S, C>(k, static_cast<const S*>(k.srcf[a])[cell], a);
     } else {
         if (cell >= k.ncell) return;
         const int y = cell / k.Nx;
@@ -301,8 +367,9 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
         relax_ct<SET, N, true, C>(k, q, f, std::make_integer_sequence<int, P>{});
     else
         relax_ct<SET, N, false, C>(k, q, f, std::make_integer_sequence<int, P>{});
+    unsigned rs = sr_seed<S, C>(k, cell);
 #pragma unroll
-    for (int a = 0; a < V; ++a) static_cast<S*>(k.dstp[a])[cell] = S(f[a]);
+    for (int a = 0; a < V; ++a) static_cast<S*>(k.dstp[a])[cell] = st_pop<S, C>(k, f[a], a, rs);
     emit_moments<C>(k, q, cell, b);
     flag_density<C>(q, b.status);
 }
@@ -346,15 +413,16 @@ k_generic(const __grid_constant__ KParams<C> k, const S* __restrict__ src,
         Kyy = fma(k.peyy[p], sum, Kyy);
     }
     const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, C(0.5) * Kxy, Kyy);
-    if (R) dst[cell] = S(fma(k.one_m_omega, value(0), k.omw_rest * q.a0));
+    unsigned rs = sr_seed<S, C>(k, cell);
+    if (R) dst[cell] = st_pop<S, C>(k, fma(k.one_m_omega, value(0), k.omw_rest * q.a0), 0, rs);
     for (int p = 0; p < P; ++p) {
         C fp = value(R + p), fm = value(R + P + p);
         if (k.force)
             pair_update<true, C>(k, q, p, fp, fm);
         else
             pair_update<false, C>(k, q, p, fp, fm);
-        dst[(long long)(R + p) * k.plane + cell] = S(fp);
-        dst[(long long)(R + P + p) * k.plane + cell] = S(fm);
+        dst[(long long)(R + p) * k.plane + cell] = st_pop<S, C>(k, fp, R + p, rs);
+        dst[(long long)(R + P + p) * k.plane + cell] = st_pop<S, C>(k, fm, R + P + p, rs);
     }
     emit_moments<C>(k, q, cell, b);
     flag_density<C>(q, b.status);
