@@ -186,6 +186,72 @@ int lbm_state_bytes(lbm_solver* s, size_t* bytes);
 int lbm_get_state(lbm_solver* s, void* host, size_t bytes);
 int lbm_set_state(lbm_solver* s, const void* host, size_t bytes);
 
+/* ---- multi-solve engine (batched channels, continuous batching) -------- */
+
+/* An engine advances many independent channel solves together: each time
+ * step is one persistent kernel launch per velocity set present, whose blocks
+ * take 128-node tiles of any resident solve from a shared work counter, so
+ * solves of uneven sizes share the GPU without one launch per solve.  A chunk
+ * of K steps (default 100) plus the per-solve fp64 reductions is captured once
+ * in a CUDA graph and replayed.  Solves can be added and removed between
+ * chunks; their populations stay resident in the engine's arena, and a solve
+ * is admitted only if its footprint (lbm_engine_solve_bytes) fits.
+ * Supported: the velocity sets with compiled kernels (the paper's D2V16,
+ * D2V32, D2V33 and the (x, z) marginals of D3V107, D3V96, D3V112;
+ * LBM_ENOTSUP otherwise), storage LBM_FP32, LBM_FP16 or LBM_BF16 (the 16-bit
+ * scale S stays 2^-6 in the engine).  Each solve's arithmetic is the one of
+ * lbm_step, so a solve's results do not depend on which other solves share
+ * the engine.  Not thread-safe. */
+typedef struct lbm_engine lbm_engine;
+
+/* Device bytes one solve occupies in an engine arena. */
+int lbm_engine_solve_bytes(const lbm_dvm* dvm, int Nx, int Ny, int precision,
+                           size_t* bytes);
+
+/* arena: caller-owned device memory of arena_bytes (256-byte aligned), or
+ * NULL to cudaMalloc arena_bytes.  The engine's control data (slot records,
+ * tile lists) is carved from the start of the arena.  max_solves: slots.
+ * stream: a cudaStream_t other than the legacy default stream, or NULL to
+ * let the engine create one (graph capture needs a non-default stream). */
+int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_bytes,
+                      void* stream, lbm_engine** out);
+void lbm_engine_destroy(lbm_engine* e);
+
+/* Admit a solve (arguments as lbm_create; rho_host as lbm_init) and
+ * initialise it.  *slot receives its slot index.  LBM_ENOMEM when no slot is
+ * free or its footprint does not fit in the arena (the caller may retry after
+ * a removal).  Synchronises the stream. */
+int lbm_engine_add(lbm_engine* e, const lbm_dvm* dvm, int order, int Nx, int Ny,
+                   double Kn, double force, const double* rho_host, int* slot);
+
+/* Release a slot and its arena memory. */
+int lbm_engine_remove(lbm_engine* e, int slot);
+
+/* Steps per chunk, even, 2..1000 (default 100). */
+int lbm_engine_set_chunk(lbm_engine* e, int steps);
+
+/* Advance every resident solve by chunks * K steps, then copy the per-slot
+ * results to `results` (host, 4 * max_solves doubles, may be NULL):
+ * results[4 s + 0] = max |u_x(t) - u_x(t - dt)| over the last step,
+ * [4 s + 1] = mdot (Eq. pf.1), [4 s + 2] = u_s (Eq. defSlip), [4 s + 3] =
+ * <u_x>; entries of free slots are stale.  Synchronises. */
+int lbm_engine_run(lbm_engine* e, int chunks, double* results);
+
+/* Time candidate launch shapes (fraction of the occupancy limit used for the
+ * persistent grid x tiles taken per grab) on the resident solves and keep
+ * the fastest.  The timed chunks advance the solves (3 chunks per candidate,
+ * counted in their step counters). */
+int lbm_engine_autotune(lbm_engine* e, double* best_ms_per_step);
+
+/* Steps done by a slot and its status (LBM_OK or LBM_ENONFINITE). */
+int lbm_engine_info(lbm_engine* e, int slot, long* steps, int* status);
+
+/* Moments of a slot's state after the last chunk (as lbm_moments). */
+int lbm_engine_moments(lbm_engine* e, int slot, double* rho, double* ux, double* uy);
+
+/* Largest contiguous free block of the arena. */
+int lbm_engine_free_bytes(lbm_engine* e, size_t* largest);
+
 /* ---- observables without allocation ------------------------------------ */
 
 /* The paper has no counterpart to this entry point; it exists for callers

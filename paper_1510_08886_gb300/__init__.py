@@ -254,3 +254,105 @@ class Solver:
         check(_lib.lib().lbm_set_state(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes),
               "lbm_set_state")
         return self
+
+
+class Engine:
+    """Many channel solves advanced together (include/lbm.h, engine section).
+
+    Solves are admitted with ``add`` (returns a slot, or None when the arena
+    or the slot table is full), advanced with ``run`` in chunks of
+    ``chunk`` steps (one CUDA-graph replay per chunk) and released with
+    ``remove``.  The arena is a torch uint8 tensor on the current device.
+    """
+
+    def __init__(self, precision="fp32", max_solves=256, arena_bytes=1 << 30, stream=None,
+                 chunk=100):
+        torch = _torch_cuda()
+        self._torch = torch
+        self.precision = precision
+        self.max_solves = int(max_solves)
+        self.arena = torch.empty(int(arena_bytes) + 256, dtype=torch.uint8, device="cuda")
+        aligned = (self.arena.data_ptr() + 255) & ~255
+        self.stream = stream
+        h = ctypes.c_void_p()
+        check(_lib.lib().lbm_engine_create(
+            PRECISIONS[precision], self.max_solves, ctypes.c_void_p(aligned), int(arena_bytes),
+            ctypes.c_void_p(stream.cuda_stream) if stream is not None else None, ctypes.byref(h)),
+            "lbm_engine_create")
+        self._h = h
+        self._dvms = {}
+        self.results = np.zeros((self.max_solves, 4))
+        self.set_chunk(chunk)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().lbm_engine_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def solve_bytes(e, w, c, Nx, Ny, precision="fp32"):
+        d = _DVM(e, w, c)
+        n = ctypes.c_size_t(0)
+        check(_lib.lib().lbm_engine_solve_bytes(d.ref(), int(Nx), int(Ny), PRECISIONS[precision],
+                                                ctypes.byref(n)), "lbm_engine_solve_bytes")
+        return n.value
+
+    def set_chunk(self, steps):
+        check(_lib.lib().lbm_engine_set_chunk(self._h, int(steps)), "lbm_engine_set_chunk")
+        self.chunk = int(steps)
+
+    def add(self, e, w, c, order, Nx, Ny, Kn, force, rho=None):
+        d = _DVM(e, w, c)
+        slot = ctypes.c_int(-1)
+        r = None
+        if rho is not None:
+            r = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(int(Ny), int(Nx)))
+        rc = _lib.lib().lbm_engine_add(self._h, d.ref(), int(order), int(Nx), int(Ny), float(Kn),
+                                       float(force), _dp(r) if r is not None else None,
+                                       ctypes.byref(slot))
+        if rc == _lib.LBM_ENOMEM:
+            return None
+        check(rc, "lbm_engine_add")
+        self._dvms[slot.value] = d
+        return slot.value
+
+    def remove(self, slot):
+        check(_lib.lib().lbm_engine_remove(self._h, int(slot)), "lbm_engine_remove")
+        self._dvms.pop(slot, None)
+
+    def run(self, chunks=1):
+        """Advance every resident solve by chunks x chunk steps; returns the
+        (max_solves, 4) array {max|du|, mdot, u_s, <u_x>} per slot."""
+        check(_lib.lib().lbm_engine_run(self._h, int(chunks), _dp(self.results)), "lbm_engine_run")
+        return self.results
+
+    def autotune(self):
+        ms = ctypes.c_double(0)
+        check(_lib.lib().lbm_engine_autotune(self._h, ctypes.byref(ms)), "lbm_engine_autotune")
+        return ms.value
+
+    def info(self, slot):
+        steps = ctypes.c_long(0)
+        st = ctypes.c_int(0)
+        check(_lib.lib().lbm_engine_info(self._h, int(slot), ctypes.byref(steps), ctypes.byref(st)),
+              "lbm_engine_info")
+        return steps.value, st.value
+
+    def moments(self, slot, Nx, Ny):
+        rho = np.empty((Ny, Nx))
+        ux = np.empty_like(rho)
+        uy = np.empty_like(rho)
+        check(_lib.lib().lbm_engine_moments(self._h, int(slot), _dp(rho), _dp(ux), _dp(uy)),
+              "lbm_engine_moments")
+        return rho, ux, uy
+
+    def free_bytes(self):
+        n = ctypes.c_size_t(0)
+        check(_lib.lib().lbm_engine_free_bytes(self._h, ctypes.byref(n)))
+        return n.value

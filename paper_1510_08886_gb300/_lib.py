@@ -55,6 +55,23 @@ SIGNATURES = {
     "lbm_state_bytes": (ctypes.c_int, [ctypes.c_void_p, c_size_p]),
     "lbm_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "lbm_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "lbm_engine_solve_bytes": (ctypes.c_int, [ctypes.POINTER(lbm_dvm), ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, c_size_p]),
+    "lbm_engine_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_size_t, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_engine_destroy": (None, [ctypes.c_void_p]),
+    "lbm_engine_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(lbm_dvm), ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, c_double_p, c_int_p]),
+    "lbm_engine_remove": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lbm_engine_set_chunk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lbm_engine_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p]),
+    "lbm_engine_autotune": (ctypes.c_int, [ctypes.c_void_p, c_double_p]),
+    "lbm_engine_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_long_p, c_int_p]),
+    "lbm_engine_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p, c_double_p,
+                                          c_double_p]),
+    "lbm_engine_free_bytes": (ctypes.c_int, [ctypes.c_void_p, c_size_p]),
     "lbm_observables_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                                ctypes.c_void_p]),

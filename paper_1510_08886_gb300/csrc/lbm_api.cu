@@ -18,25 +18,25 @@
 using lbm::DevBufs;
 using lbm::KParams;
 
-struct lbm_solver {
-    int precision = LBM_FP64;
-    int N = 3, Nx = 1, Ny = 1, V = 0, R = 0, P = 0, maxey = 0, maxex = 0, set_id = -1;
-    double c = 1, Kn = 0, tau = 0, dt = 0, g = 0, den = 0;
-    double scale = 1.0 / 64.0;   // S of the 16-bit storage (power of 2)
+struct lbm_solver : lbm::SolveSpec {
     cudaStream_t stream = nullptr;
     bool owns = false;
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    size_t elem = 8;
     DevBufs b{};
     int cur = 0;
     long steps = 0;
-    std::vector<int> perm;       // internal plane -> caller velocity index
-    std::vector<int> ex, ey;     // internal order
-    std::vector<double> w;
     KParams<double> k64{};
     KParams<float> k32{};
 };
+
+namespace lbm {
+size_t elem_bytes(int precision) {
+    return precision == LBM_FP64 ? 8 : precision == LBM_FP32 ? 4 : 2;
+}
+}  // namespace lbm
+
+using lbm::elem_bytes;
 
 namespace {
 
@@ -51,9 +51,6 @@ struct StateHeader {
 
 size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
-size_t elem_bytes(int precision) {
-    return precision == LBM_FP64 ? 8 : precision == LBM_FP32 ? 4 : 2;
-}
 
 bool valid_precision(int p) { return p >= LBM_FP64 && p <= LBM_BF16; }
 bool is16(int p) { return p == LBM_FP16 || p == LBM_BF16; }
@@ -168,7 +165,7 @@ int canonicalize(const lbm_dvm* d, std::vector<int>& ex, std::vector<int>& ey,
 }
 
 template <typename C>
-void fill_params(const lbm_solver* s, KParams<C>& k) {
+void fill_params_impl(const lbm::SolveSpec* s, KParams<C>& k) {
     std::memset(&k, 0, sizeof(k));
     k.Nx = s->Nx;
     k.Ny = s->Ny;
@@ -370,7 +367,7 @@ int launch_init(lbm_solver* s, const double* rho_dev) {
     if (e != cudaSuccess) return cuda_status(e);
     if (is16(s->precision) && s->scale != 1.0 / 64.0) {
         s->scale = 1.0 / 64.0;
-        fill_params(s, s->k32);
+        lbm::fill_params(*s, s->k32);
     }
     if (s->precision == LBM_FP64) {
         s->k64.emit = 1;
@@ -427,7 +424,7 @@ int refresh_scale(lbm_solver* s) {
     e = lbm::launch_rescale_fp16(s->b.f[s->cur], n, bf, float(s->scale / ns), s->stream);
     if (e != cudaSuccess) return cuda_status(e);
     s->scale = ns;
-    fill_params(s, s->k32);
+    lbm::fill_params(*s, s->k32);
     return LBM_OK;
 }
 
@@ -436,38 +433,11 @@ int create_common(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, doub
                   lbm_solver** out) {
     if (!out) return LBM_EINVAL;
     *out = nullptr;
-    if (!valid_precision(precision)) return LBM_EINVAL;
-    if (Nx < 1 || Ny < 1 || !(Kn > 0) || !std::isfinite(Kn) || !std::isfinite(force))
-        return LBM_EINVAL;
-    if ((long long)Nx * Ny > (long long)0x7fffffff) return LBM_EINVAL;
     lbm_solver* s = new (std::nothrow) lbm_solver();
     if (!s) return LBM_ENOMEM;
-    int rc = canonicalize(dvm, s->ex, s->ey, s->w, s->perm, s->R, s->P, s->set_id);
+    int rc = lbm::prepare_spec(dvm, order, Nx, Ny, Kn, force, precision, *s);
     if (rc) { delete s; return rc; }
-    int Q = -1;
-    lbm_dvm_quadrature_order(dvm, &Q);
-    if (order < 2 || order > 4 || Q < 5 || Q < 2 * order - 1) { delete s; return LBM_EDEGREE; }
-    s->V = dvm->V;
-    s->maxey = 0;
-    for (int a = 0; a < s->V; ++a) {
-        s->maxey = std::max(s->maxey, std::abs(s->ey[a]));
-        s->maxex = std::max(s->maxex, std::abs(s->ex[a]));
-    }
-    if (Ny < s->maxey || s->maxey == 0) { delete s; return LBM_EINVAL; }
-    s->precision = precision;
-    s->N = order;
-    s->Nx = Nx;
-    s->Ny = Ny;
-    s->c = dvm->c;
-    s->Kn = Kn;
-    s->tau = std::sqrt(2.0 / M_PI) * Kn;    // Eq. nm.13
-    s->dt = (1.0 / Ny) / dvm->c;            // dx = l0 / Ny, one hop per step
-    s->g = force;
-    s->den = 0.0;
-    for (int a = 0; a < s->V; ++a)
-        if (s->ey[a] > 0) s->den += s->ey[a] * s->w[a];
     s->stream = static_cast<cudaStream_t>(stream);
-    s->elem = elem_bytes(precision);
     const Layout L = layout(s->V, size_t(Nx) * Ny, s->elem);
     if (own) {
         cudaError_t e = cudaMalloc(&s->ws, L.total);
@@ -491,13 +461,57 @@ int create_common(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, doub
     s->b.partial = reinterpret_cast<double*>(base + L.partial);
     s->b.results = reinterpret_cast<double*>(base + L.results);
     s->b.status = reinterpret_cast<unsigned*>(base + L.status);
-    fill_params(s, s->k64);
-    fill_params(s, s->k32);
+    lbm::fill_params(*s, s->k64);
+    lbm::fill_params(*s, s->k32);
     *out = s;
     return LBM_OK;
 }
 
 }  // namespace
+
+namespace lbm {
+
+int prepare_spec(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, double force,
+                 int precision, SolveSpec& s) {
+    if (!valid_precision(precision)) return LBM_EINVAL;
+    if (Nx < 1 || Ny < 1 || !(Kn > 0) || !std::isfinite(Kn) || !std::isfinite(force))
+        return LBM_EINVAL;
+    if ((long long)Nx * Ny > (long long)0x7fffffff) return LBM_EINVAL;
+    int rc = canonicalize(dvm, s.ex, s.ey, s.w, s.perm, s.R, s.P, s.set_id);
+    if (rc) return rc;
+    int Q = -1;
+    lbm_dvm_quadrature_order(dvm, &Q);
+    if (order < 2 || order > 4 || Q < 5 || Q < 2 * order - 1) return LBM_EDEGREE;
+    s.V = dvm->V;
+    s.maxey = s.maxex = 0;
+    for (int a = 0; a < s.V; ++a) {
+        s.maxey = std::max(s.maxey, std::abs(s.ey[a]));
+        s.maxex = std::max(s.maxex, std::abs(s.ex[a]));
+    }
+    if (Ny < s.maxey || s.maxey == 0) return LBM_EINVAL;
+    s.precision = precision;
+    s.N = order;
+    s.Nx = Nx;
+    s.Ny = Ny;
+    s.c = dvm->c;
+    s.Kn = Kn;
+    s.tau = std::sqrt(2.0 / M_PI) * Kn;    // Eq. nm.13
+    s.dt = (1.0 / Ny) / dvm->c;            // dx = l0 / Ny, one hop per step
+    s.g = force;
+    s.den = 0.0;
+    for (int a = 0; a < s.V; ++a)
+        if (s.ey[a] > 0) s.den += s.ey[a] * s.w[a];
+    s.elem = elem_bytes(precision);
+    s.scale = 1.0 / 64.0;
+    return LBM_OK;
+}
+
+template <typename C>
+void fill_params(const SolveSpec& s, KParams<C>& k) { fill_params_impl(&s, k); }
+template void fill_params<float>(const SolveSpec&, KParams<float>&);
+template void fill_params<double>(const SolveSpec&, KParams<double>&);
+
+}  // namespace lbm
 
 extern "C" {
 
@@ -714,7 +728,7 @@ int lbm_set_state(lbm_solver* s, const void* host, size_t bytes) {
     s->steps = h.steps;
     if (is16(s->precision)) {
         s->scale = h.scale;
-        fill_params(s, s->k32);
+        lbm::fill_params(*s, s->k32);
     }
     return LBM_OK;
 }

@@ -1,0 +1,547 @@
+// Host side of the multi-solve engine (include/lbm.h, "engine" section):
+// a device arena with first-fit allocation (admission by footprint), slots
+// that can be added and removed between chunks, per-velocity-set tile lists,
+// CUDA-graph capture of a chunk of time steps plus the per-solve reductions,
+// and an autotuner of the persistent grid size and the tiles taken per grab.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "engine_launch.cuh"
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+cudaError_t engine_step_fp32(int set_id, int N, const EngineLaunch& L, cudaStream_t st);
+cudaError_t engine_step_fp16(int set_id, int N, bool bf16, const EngineLaunch& L, cudaStream_t st);
+int engine_occupancy_fp32(int set_id, int N);
+int engine_occupancy_fp16(int set_id, int N, bool bf16);
+cudaError_t engine_reduce(const void* solves, const int* active, double* out, int nslots,
+                          cudaStream_t st);
+cudaError_t engine_advance(unsigned int* seed, unsigned int by, cudaStream_t st);
+}  // namespace lbm
+
+namespace {
+
+constexpr int kGroups = 18;        // 6 compiled velocity sets x Hermite orders 2..4
+constexpr int kMaxChunk = 1000;    // steps per captured chunk
+
+size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// First-fit allocator over [0, size) with 256-byte granularity.
+class Arena {
+  public:
+    void reset(size_t size) {
+        free_.clear();
+        if (size) free_[0] = size;
+    }
+    bool alloc(size_t n, size_t& off) {
+        n = al256(n);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            off = it->first;
+            const size_t rest = it->second - n, o2 = it->first + n;
+            free_.erase(it);
+            if (rest) free_[o2] = rest;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        n = al256(n);
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t largest() const {
+        size_t m = 0;
+        for (const auto& kv : free_) m = std::max(m, kv.second);
+        return m;
+    }
+
+  private:
+    std::map<size_t, size_t> free_;
+};
+
+struct SlotLayout {
+    size_t f0, f1, rho, ux, uy, prev, total;
+};
+
+SlotLayout slot_layout(int V, size_t ncell, size_t elem) {
+    SlotLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t n) { size_t o = off; off = al256(off + n); return o; };
+    L.f0 = take(size_t(V) * ncell * elem);
+    L.f1 = take(size_t(V) * ncell * elem);
+    L.rho = take(ncell * 8);
+    L.ux = take(ncell * 8);
+    L.uy = take(ncell * 8);
+    L.prev = take(ncell * 8);
+    L.total = off;
+    return L;
+}
+
+struct EngSlot {
+    bool used = false;
+    lbm::SolveSpec spec;
+    size_t off = 0, bytes = 0;
+    long steps = 0;
+    int group = -1;
+};
+
+int cuda_rc(cudaError_t e) {
+    return e == cudaSuccess ? LBM_OK : (e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
+}
+
+}  // namespace
+
+struct lbm_engine {
+    int precision = LBM_FP32;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false, own_arena = false;
+    char* base = nullptr;
+    size_t bytes = 0, ctrl = 0;
+    Arena arena;                               // over [ctrl, bytes)
+    int max_slots = 0;
+    size_t tile_cap = 0;
+    lbm::EngineSolve<float>* d_solves = nullptr;
+    int* d_active = nullptr;
+    double* d_results = nullptr;
+    unsigned* d_status = nullptr;
+    int* d_ntiles = nullptr;
+    int* d_counters = nullptr;
+    unsigned* d_seed = nullptr;
+    lbm::EngineTile* d_tiles = nullptr;
+    std::vector<EngSlot> slots;
+    std::vector<lbm::EngineSolve<float>> h_solves;
+    std::vector<int> h_active;
+    std::vector<double> h_results;
+    int K = 100;
+    double bps_factor = 1.0;   // fraction of the occupancy limit used for the grid
+    int grab = 4;              // tiles taken per atomic grab
+    int sms = 0;
+    bool tiles_dirty = true, graph_dirty = true;
+    std::vector<int> groups, group_off;        // present groups and their tile offsets
+    std::vector<int> grids;                    // persistent grid size per present group
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int group_of(const lbm::SolveSpec& s) { return s.set_id * 3 + (s.N - 2); }
+
+bool is16(int p) { return p == LBM_FP16 || p == LBM_BF16; }
+
+int occupancy(const lbm_engine* e, int group) {
+    const int set = group / 3, N = group % 3 + 2;
+    const int b = is16(e->precision) ? lbm::engine_occupancy_fp16(set, N, e->precision == LBM_BF16)
+                                     : lbm::engine_occupancy_fp32(set, N);
+    return std::max(1, b);
+}
+
+int rebuild_tiles(lbm_engine* e) {
+    std::vector<lbm::EngineTile> t;
+    std::vector<int> groups, offs;
+    std::vector<int> counts(kGroups, 0);
+    for (int g = 0; g < kGroups; ++g) {
+        const size_t start = t.size();
+        for (int s = 0; s < e->max_slots; ++s) {
+            const EngSlot& sl = e->slots[s];
+            if (!sl.used || sl.group != g) continue;
+            const int n = sl.spec.Nx * sl.spec.Ny;
+            for (int c0 = 0; c0 < n; c0 += lbm::kBlock) t.push_back({s, c0});
+        }
+        if (t.size() > start) {
+            groups.push_back(g);
+            offs.push_back(int(start));
+            counts[g] = int(t.size() - start);
+        }
+    }
+    if (t.size() > e->tile_cap) return LBM_ENOMEM;
+    cudaError_t err = cudaSuccess;
+    if (!t.empty())
+        err = cudaMemcpyAsync(e->d_tiles, t.data(), t.size() * sizeof(lbm::EngineTile),
+                              cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(e->d_ntiles, counts.data(), kGroups * sizeof(int),
+                              cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    if (err != cudaSuccess) return cuda_rc(err);
+    if (groups != e->groups) e->graph_dirty = true;
+    e->groups = groups;
+    e->group_off = offs;
+    e->tiles_dirty = false;
+    return LBM_OK;
+}
+
+// One chunk of K steps + the reductions + the seed advance, on the stream.
+int enqueue_chunk(lbm_engine* e) {
+    cudaError_t err = cudaMemsetAsync(e->d_counters, 0, sizeof(int) * kGroups * e->K, e->stream);
+    if (err != cudaSuccess) return cuda_rc(err);
+    for (int i = 0; i < e->K; ++i) {
+        for (size_t gi = 0; gi < e->groups.size(); ++gi) {
+            const int g = e->groups[gi];
+            lbm::EngineLaunch L{};
+            L.solves = e->d_solves;
+            L.tiles = e->d_tiles + e->group_off[gi];
+            L.ntiles = e->d_ntiles + g;
+            L.counter = e->d_counters + i * kGroups + g;
+            L.seed = e->d_seed;
+            L.parity = i & 1;
+            L.emit = i == e->K - 1 ? 1 : (i == e->K - 2 ? 2 : 0);
+            L.chunk = e->grab;
+            L.grid = e->grids[gi];
+            const int set = g / 3, N = g % 3 + 2;
+            err = is16(e->precision)
+                      ? lbm::engine_step_fp16(set, N, e->precision == LBM_BF16, L, e->stream)
+                      : lbm::engine_step_fp32(set, N, L, e->stream);
+            if (err != cudaSuccess) return cuda_rc(err);
+        }
+    }
+    err = lbm::engine_reduce(e->d_solves, e->d_active, e->d_results, e->max_slots, e->stream);
+    if (err == cudaSuccess) err = lbm::engine_advance(e->d_seed, unsigned(e->K), e->stream);
+    return cuda_rc(err);
+}
+
+int recapture(lbm_engine* e) {
+    e->grids.clear();
+    for (int g : e->groups)
+        e->grids.push_back(std::max(1, int(std::lround(occupancy(e, g) * e->bps_factor))) * e->sms);
+    if (e->exec) {
+        cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t err = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return cuda_rc(err);
+    const int rc = enqueue_chunk(e);
+    err = cudaStreamEndCapture(e->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (err != cudaSuccess) return cuda_rc(err);
+    err = cudaGraphInstantiate(&e->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return cuda_rc(err);
+    e->graph_dirty = false;
+    return LBM_OK;
+}
+
+int prepare(lbm_engine* e) {
+    if (e->tiles_dirty) {
+        const int rc = rebuild_tiles(e);
+        if (rc) return rc;
+    }
+    if (e->graph_dirty && !e->groups.empty()) return recapture(e);
+    return LBM_OK;
+}
+
+int fetch_results(lbm_engine* e, double* out) {
+    cudaError_t err = cudaMemcpyAsync(e->h_results.data(), e->d_results,
+                                      sizeof(double) * 4 * e->max_slots, cudaMemcpyDeviceToHost,
+                                      e->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    if (err != cudaSuccess) return cuda_rc(err);
+    if (out) std::memcpy(out, e->h_results.data(), sizeof(double) * 4 * e->max_slots);
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_engine_solve_bytes(const lbm_dvm* dvm, int Nx, int Ny, int precision, size_t* bytes) {
+    if (!dvm || !bytes || Nx < 1 || Ny < 1 || dvm->V < 1 || dvm->V > LBM_MAX_V) return LBM_EINVAL;
+    if (precision != LBM_FP32 && !is16(precision)) return LBM_EINVAL;
+    *bytes = slot_layout(dvm->V, size_t(Nx) * Ny, lbm::elem_bytes(precision)).total;
+    return LBM_OK;
+}
+
+int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_bytes, void* stream,
+                      lbm_engine** out) {
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    if ((precision != LBM_FP32 && !is16(precision)) || max_solves < 1 || max_solves > 65536)
+        return LBM_EINVAL;
+    if (arena && (reinterpret_cast<uintptr_t>(arena) & 255)) return LBM_EINVAL;
+    lbm_engine* e = new (std::nothrow) lbm_engine();
+    if (!e) return LBM_ENOMEM;
+    e->precision = precision;
+    e->max_slots = max_solves;
+    const size_t elem = lbm::elem_bytes(precision);
+    // tiles: at most one per 128 nodes of the smallest lattice that fits, plus a
+    // partial tile per solve
+    const size_t max_cells = arena_bytes / (2 * 16 * elem);
+    e->tile_cap = max_cells / lbm::kBlock + size_t(max_solves) + 1;
+    size_t off = 0;
+    auto take = [&](size_t n) { size_t o = off; off = al256(off + n); return o; };
+    const size_t o_solves = take(sizeof(lbm::EngineSolve<float>) * max_solves);
+    const size_t o_active = take(sizeof(int) * max_solves);
+    const size_t o_results = take(sizeof(double) * 4 * max_solves);
+    const size_t o_status = take(sizeof(unsigned) * max_solves);
+    const size_t o_ntiles = take(sizeof(int) * kGroups);
+    const size_t o_counters = take(sizeof(int) * kGroups * kMaxChunk);
+    const size_t o_seed = take(sizeof(unsigned));
+    const size_t o_tiles = take(sizeof(lbm::EngineTile) * e->tile_cap);
+    e->ctrl = off;
+    if (arena_bytes <= e->ctrl) { delete e; return LBM_ENOMEM; }
+    if (arena) {
+        e->base = static_cast<char*>(arena);
+    } else {
+        if (cudaMalloc(&e->base, arena_bytes) != cudaSuccess) { delete e; return LBM_ENOMEM; }
+        e->own_arena = true;
+    }
+    e->bytes = arena_bytes;
+    e->arena.reset(arena_bytes - e->ctrl);
+    e->d_solves = reinterpret_cast<lbm::EngineSolve<float>*>(e->base + o_solves);
+    e->d_active = reinterpret_cast<int*>(e->base + o_active);
+    e->d_results = reinterpret_cast<double*>(e->base + o_results);
+    e->d_status = reinterpret_cast<unsigned*>(e->base + o_status);
+    e->d_ntiles = reinterpret_cast<int*>(e->base + o_ntiles);
+    e->d_counters = reinterpret_cast<int*>(e->base + o_counters);
+    e->d_seed = reinterpret_cast<unsigned*>(e->base + o_seed);
+    e->d_tiles = reinterpret_cast<lbm::EngineTile*>(e->base + o_tiles);
+    e->slots.resize(max_solves);
+    e->h_solves.resize(max_solves);
+    e->h_active.assign(max_solves, 0);
+    e->h_results.assign(4 * size_t(max_solves), 0.0);
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) {
+        if (stream) {
+            e->stream = static_cast<cudaStream_t>(stream);
+        } else {
+            err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+            e->own_stream = err == cudaSuccess;
+        }
+    }
+    if (err == cudaSuccess) err = cudaMemsetAsync(e->base, 0, e->ctrl, e->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    if (err != cudaSuccess) {
+        lbm_engine_destroy(e);
+        return cuda_rc(err);
+    }
+    *out = e;
+    return LBM_OK;
+}
+
+void lbm_engine_destroy(lbm_engine* e) {
+    if (!e) return;
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->own_arena && e->base) cudaFree(e->base);
+    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+    delete e;
+}
+
+int lbm_engine_add(lbm_engine* e, const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn,
+                   double force, const double* rho_host, int* slot_out) {
+    if (!e || !slot_out) return LBM_EINVAL;
+    lbm::SolveSpec spec;
+    int rc = lbm::prepare_spec(dvm, order, Nx, Ny, Kn, force, e->precision, spec);
+    if (rc) return rc;
+    if (spec.set_id < 0) return LBM_ENOTSUP;       // only compiled velocity sets
+    int slot = -1;
+    for (int s = 0; s < e->max_slots; ++s)
+        if (!e->slots[s].used) { slot = s; break; }
+    if (slot < 0) return LBM_ENOMEM;
+    const SlotLayout L = slot_layout(spec.V, size_t(Nx) * Ny, spec.elem);
+    size_t off = 0;
+    if (!e->arena.alloc(L.total, off)) return LBM_ENOMEM;
+    char* b = e->base + e->ctrl + off;
+    EngSlot& sl = e->slots[slot];
+    sl.used = true;
+    sl.spec = spec;
+    sl.off = off;
+    sl.bytes = L.total;
+    sl.steps = 0;
+    sl.group = group_of(spec);
+    lbm::EngineSolve<float>& h = e->h_solves[slot];
+    std::memset(&h, 0, sizeof(h));
+    lbm::fill_params(spec, h.k);
+    h.f[0] = b + L.f0;
+    h.f[1] = b + L.f1;
+    h.rho = reinterpret_cast<double*>(b + L.rho);
+    h.ux = reinterpret_cast<double*>(b + L.ux);
+    h.uy = reinterpret_cast<double*>(b + L.uy);
+    h.prev = reinterpret_cast<double*>(b + L.prev);
+    h.status = e->d_status + slot;
+    h.phase = 0;
+    h.kn = Kn;
+    h.tau = spec.tau;
+    h.g = force;
+    // initial state fbar = rho w, first relaxation, moments (shared init kernel)
+    lbm::DevBufs db{};
+    db.f[0] = h.f[0];
+    db.f[1] = h.f[1];
+    db.rho = h.rho;
+    db.ux = h.ux;
+    db.uy = h.uy;
+    db.prev_ux = h.prev;
+    db.status = h.status;
+    const int n = Nx * Ny;
+    cudaError_t err = cudaMemcpyAsync(e->d_solves + slot, &h, sizeof(h), cudaMemcpyHostToDevice,
+                                      e->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(h.status, 0, sizeof(unsigned), e->stream);
+    if (err == cudaSuccess) {
+        if (rho_host) {
+            err = cudaMemcpyAsync(h.prev, rho_host, size_t(n) * 8, cudaMemcpyHostToDevice, e->stream);
+        } else {
+            std::vector<double> ones(n, 1.0);
+            err = cudaMemcpyAsync(h.prev, ones.data(), size_t(n) * 8, cudaMemcpyHostToDevice,
+                                  e->stream);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+        }
+    }
+    if (err == cudaSuccess) {
+        lbm::KParams<float> k = h.k;
+        k.emit = 1;
+        k.seed = 0u;
+        err = is16(e->precision)
+                  ? lbm::launch_init_fp16(k, spec.N, e->precision == LBM_BF16, h.prev, h.f[0], db,
+                                          e->stream)
+                  : lbm::launch_init_fp32(k, spec.N, h.prev, h.f[0], db, e->stream);
+    }
+    e->h_active[slot] = 1;
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(e->d_active + slot, &e->h_active[slot], sizeof(int),
+                              cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    if (err != cudaSuccess) {
+        e->h_active[slot] = 0;
+        sl.used = false;
+        e->arena.release(off, L.total);
+        return cuda_rc(err);
+    }
+    e->tiles_dirty = true;
+    *slot_out = slot;
+    return LBM_OK;
+}
+
+int lbm_engine_remove(lbm_engine* e, int slot) {
+    if (!e || slot < 0 || slot >= e->max_slots || !e->slots[slot].used) return LBM_EINVAL;
+    EngSlot& sl = e->slots[slot];
+    e->h_active[slot] = 0;
+    cudaError_t err = cudaMemcpyAsync(e->d_active + slot, &e->h_active[slot], sizeof(int),
+                                      cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    if (err != cudaSuccess) return cuda_rc(err);
+    e->arena.release(sl.off, sl.bytes);
+    sl.used = false;
+    e->tiles_dirty = true;
+    return LBM_OK;
+}
+
+int lbm_engine_set_chunk(lbm_engine* e, int steps) {
+    if (!e || steps < 2 || steps > kMaxChunk || (steps & 1)) return LBM_EINVAL;
+    if (steps != e->K) {
+        e->K = steps;
+        e->graph_dirty = true;
+    }
+    return LBM_OK;
+}
+
+int lbm_engine_run(lbm_engine* e, int chunks, double* results) {
+    if (!e || chunks < 0) return LBM_EINVAL;
+    int rc = prepare(e);
+    if (rc) return rc;
+    if (!e->groups.empty()) {
+        for (int c = 0; c < chunks; ++c) {
+            const cudaError_t err = cudaGraphLaunch(e->exec, e->stream);
+            if (err != cudaSuccess) return cuda_rc(err);
+        }
+        for (auto& sl : e->slots)
+            if (sl.used) sl.steps += long(chunks) * e->K;
+    }
+    return fetch_results(e, results);
+}
+
+int lbm_engine_autotune(lbm_engine* e, double* best_ms_per_step) {
+    if (!e) return LBM_EINVAL;
+    int rc = prepare(e);
+    if (rc) return rc;
+    if (e->groups.empty()) return LBM_OK;
+    const double factors[] = {1.0, 0.5};
+    const int grabs[] = {1, 2, 4, 8, 16};
+    double best = HUGE_VAL, bf = e->bps_factor;
+    int bg = e->grab;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return LBM_ECUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return LBM_ECUDA; }
+    for (double f : factors) {
+        for (int g : grabs) {
+            e->bps_factor = f;
+            e->grab = g;
+            if ((rc = recapture(e))) break;
+            cudaGraphLaunch(e->exec, e->stream);      // warm-up chunk
+            cudaEventRecord(a, e->stream);
+            cudaGraphLaunch(e->exec, e->stream);
+            cudaGraphLaunch(e->exec, e->stream);
+            cudaEventRecord(b, e->stream);
+            if (cudaEventSynchronize(b) != cudaSuccess) { rc = LBM_ECUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            for (auto& sl : e->slots)
+                if (sl.used) sl.steps += 3L * e->K;
+            if (ms < best) { best = ms; bf = f; bg = g; }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) return rc;
+    e->bps_factor = bf;
+    e->grab = bg;
+    rc = recapture(e);
+    if (best_ms_per_step) *best_ms_per_step = best / (2.0 * e->K);
+    return rc;
+}
+
+int lbm_engine_info(lbm_engine* e, int slot, long* steps, int* status) {
+    if (!e || slot < 0 || slot >= e->max_slots || !e->slots[slot].used) return LBM_EINVAL;
+    if (steps) *steps = e->slots[slot].steps;
+    if (status) {
+        unsigned st = 0;
+        cudaError_t err = cudaMemcpyAsync(&st, e->d_status + slot, sizeof(st), cudaMemcpyDeviceToHost,
+                                          e->stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+        if (err != cudaSuccess) return cuda_rc(err);
+        *status = st ? LBM_ENONFINITE : LBM_OK;
+    }
+    return LBM_OK;
+}
+
+int lbm_engine_moments(lbm_engine* e, int slot, double* rho, double* ux, double* uy) {
+    if (!e || slot < 0 || slot >= e->max_slots || !e->slots[slot].used) return LBM_EINVAL;
+    const lbm::EngineSolve<float>& h = e->h_solves[slot];
+    const size_t n = size_t(e->slots[slot].spec.Nx) * e->slots[slot].spec.Ny * 8;
+    cudaError_t err = cudaSuccess;
+    if (rho) err = cudaMemcpyAsync(rho, h.rho, n, cudaMemcpyDeviceToHost, e->stream);
+    if (ux && err == cudaSuccess) err = cudaMemcpyAsync(ux, h.ux, n, cudaMemcpyDeviceToHost, e->stream);
+    if (uy && err == cudaSuccess) err = cudaMemcpyAsync(uy, h.uy, n, cudaMemcpyDeviceToHost, e->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    return cuda_rc(err);
+}
+
+int lbm_engine_free_bytes(lbm_engine* e, size_t* largest) {
+    if (!e || !largest) return LBM_EINVAL;
+    *largest = e->arena.largest();
+    return LBM_OK;
+}
+
+}  // extern "C"

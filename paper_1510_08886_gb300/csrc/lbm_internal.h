@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "lbm.h"
 
 namespace lbm {
@@ -97,5 +99,25 @@ cudaError_t launch_absmax_fp16(const void* f, long long n, bool bf16, float* out
 // multiply every stored value by `factor` (a power of 2)
 cudaError_t launch_rescale_fp16(void* f, long long n, bool bf16, float factor,
                                 cudaStream_t st);
+
+// Validated, canonicalised description of one channel solve (shared by the
+// single-solve API and the engine).
+struct SolveSpec {
+    int precision = LBM_FP64;
+    int N = 3, Nx = 1, Ny = 1, V = 0, R = 0, P = 0, maxey = 0, maxex = 0, set_id = -1;
+    double c = 1, Kn = 0, tau = 0, dt = 0, g = 0, den = 0;
+    double scale = 1.0 / 64.0;   // S of the 16-bit storage (power of 2)
+    size_t elem = 8;
+    std::vector<int> perm;       // internal plane -> caller velocity index
+    std::vector<int> ex, ey;     // internal order
+    std::vector<double> w;
+};
+
+// Validate the arguments of lbm_create and fill `s` (LBM_OK or an error code).
+int prepare_spec(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, double force,
+                 int precision, SolveSpec& s);
+template <typename C>
+void fill_params(const SolveSpec& s, KParams<C>& k);
+size_t elem_bytes(int precision);
 
 }  // namespace lbm

@@ -77,8 +77,8 @@ __device__ __forceinline__ unsigned mix32(unsigned x) {   // integer hash (xorsh
 }
 
 template <typename S, typename C>
-__device__ __forceinline__ unsigned sr_seed(const KParams<C>& k, int cell) {
-    if constexpr (Storage<S>::scaled) return mix32(unsigned(cell) ^ mix32(k.seed * 0x9e3779b9u + 1u));
+__device__ __forceinline__ unsigned sr_seed(unsigned seed, int cell) {
+    if constexpr (Storage<S>::scaled) return mix32(unsigned(cell) ^ mix32(seed * 0x9e3779b9u + 1u));
     else return 0u;
 }
 
@@ -367,7 +367,7 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
         relax_ct<SET, N, true, C>(k, q, f, std::make_integer_sequence<int, P>{});
     else
         relax_ct<SET, N, false, C>(k, q, f, std::make_integer_sequence<int, P>{});
-    unsigned rs = sr_seed<S, C>(k, cell);
+    unsigned rs = sr_seed<S, C>(k.seed, cell);
 #pragma unroll
     for (int a = 0; a < V; ++a) static_cast<S*>(k.dstp[a])[cell] = st_pop<S, C>(k, f[a], a, rs);
     emit_moments<C>(k, q, cell, b);
@@ -413,7 +413,7 @@ k_generic(const __grid_constant__ KParams<C> k, const S* __restrict__ src,
         Kyy = fma(k.peyy[p], sum, Kyy);
     }
     const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, C(0.5) * Kxy, Kyy);
-    unsigned rs = sr_seed<S, C>(k, cell);
+    unsigned rs = sr_seed<S, C>(k.seed, cell);
     if (R) dst[cell] = st_pop<S, C>(k, fma(k.one_m_omega, value(0), k.omw_rest * q.a0), 0, rs);
     for (int p = 0; p < P; ++p) {
         C fp = value(R + p), fm = value(R + P + p);

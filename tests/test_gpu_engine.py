@@ -1,0 +1,178 @@
+"""Multi-solve engine: batched channels of uneven sizes and different velocity
+sets in one persistent launch per set, CUDA-graph chunks, admission by arena
+footprint, continuous add/remove.
+
+Key property: a solve's arithmetic does not depend on the other solves in
+the engine -- results alone and in the mix are bit-identical, and identical
+to the single-solve API (same per-node code, deterministic per-solve
+reductions)."""
+import numpy as np
+import pytest
+
+import oracle
+from lbm_inputs import batch_workload, rho_field
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build_library()
+
+
+MIX = [("D2V33", 4, 256, 40, 0.05), ("D3V107xz", 3, 64, 33, 0.3), ("D2V33", 4, 1, 77, 1.0),
+       ("D2V16", 3, 1, 64, 0.1), ("D3V107xz", 3, 256, 20, 0.01), ("D2V32", 3, 5, 30, 0.2),
+       ("D2V33", 4, 64, 129, 0.5), ("D3V96xz", 3, 17, 14, 0.7)]
+
+
+def _add(eng, spec, seed):
+    import paper_1510_08886_gb300 as lbm
+    name, N, Nx, Ny, Kn = spec
+    e, w, c = lbm.dvm(name)
+    return eng.add(e, w, c, N, Nx, Ny, Kn, oracle.force_for_mach(Kn, 1e-2),
+                   rho=rho_field(Nx, Ny, seed=seed))
+
+
+def test_alone_vs_mix_bitwise_and_vs_single_solver():
+    import paper_1510_08886_gb300 as lbm
+    mix = lbm.Engine("fp32", max_solves=16, arena_bytes=256 << 20, chunk=50)
+    slots = [_add(mix, s, seed=i + 1) for i, s in enumerate(MIX)]
+    res_mix = mix.run(2).copy()
+    for i, spec in enumerate(MIX):
+        name, N, Nx, Ny, Kn = spec
+        alone = lbm.Engine("fp32", max_solves=2, arena_bytes=64 << 20, chunk=50)
+        s = _add(alone, spec, seed=i + 1)
+        res_alone = alone.run(2)
+        m_mix = mix.moments(slots[i], Nx, Ny)
+        m_alone = alone.moments(s, Nx, Ny)
+        for a, b in zip(m_mix, m_alone):
+            assert np.array_equal(a, b)
+        assert np.array_equal(res_mix[slots[i]], res_alone[s])
+        # the single-solve API runs the same arithmetic
+        e, w, c = lbm.dvm(name)
+        single = lbm.Solver(e, w, c, N, Nx, Ny, Kn, oracle.force_for_mach(Kn, 1e-2),
+                            precision="fp32").init(rho_field(Nx, Ny, seed=i + 1)).step(100)
+        r, ux, uy = single.moments()
+        assert np.max(np.abs(ux - m_mix[1])) <= 1e-6 * np.max(np.abs(ux))
+        assert np.max(np.abs(r - m_mix[0])) <= 1e-6
+        alone.close()
+        assert mix.info(slots[i]) == (100, 0)
+
+
+def test_engine_vs_oracle_steady_state():
+    """Config-1 channel run to steady state inside a busy engine."""
+    import paper_1510_08886_gb300 as lbm
+    eng = lbm.Engine("fp32", max_solves=8, arena_bytes=128 << 20)
+    others = [_add(eng, s, seed=5) for s in MIX[:3]]
+    e, w, c = lbm.dvm("D2V16")
+    Kn = 0.1
+    g = oracle.force_for_mach(Kn)
+    slot = eng.add(e, w, c, 3, 1, 64, Kn, g)
+    for _ in range(100):
+        res = eng.run(1)
+        if res[slot, 0] < 1e-10:
+            break
+    assert res[slot, 0] < 1e-10
+    ref = oracle.channel("D2V16", 3, 1, 64, Kn, g).init()
+    ref.run_to_steady(1e-10, 50000)
+    assert abs(res[slot, 1] / ref.mass_flow() - 1) < 1e-4
+    assert abs(res[slot, 2] / ref.slip_velocity() - 1) < 1e-4
+    assert abs(res[slot, 3] / ref.mean_ux() - 1) < 1e-4
+    assert len(others) == 3
+
+
+def test_admission_by_footprint_and_reuse():
+    import paper_1510_08886_gb300 as lbm
+    e, w, c = lbm.dvm("D2V33")
+    per = lbm.Engine.solve_bytes(e, w, c, 256, 256, "fp32")
+    eng = lbm.Engine("fp32", max_solves=64, arena_bytes=3 * per + (8 << 20))
+    free0 = eng.free_bytes()
+    slots = []
+    while True:
+        s = eng.add(e, w, c, 4, 256, 256, 0.1, 1e-3)
+        if s is None:
+            break
+        slots.append(s)
+    assert len(slots) >= 3
+    eng.run(1)
+    eng.remove(slots[1])
+    s = eng.add(e, w, c, 4, 256, 256, 0.1, 1e-3)
+    assert s is not None
+    assert eng.add(e, w, c, 4, 256, 256, 0.1, 1e-3) is None
+    for x in slots[:1] + slots[2:] + [s]:
+        eng.remove(x)
+    assert eng.free_bytes() == free0
+
+
+def test_remove_then_add_does_not_disturb_others():
+    import paper_1510_08886_gb300 as lbm
+    a = lbm.Engine("fp32", max_solves=8, arena_bytes=128 << 20, chunk=20)
+    b = lbm.Engine("fp32", max_solves=8, arena_bytes=128 << 20, chunk=20)
+    keep_a = _add(a, MIX[0], seed=3)
+    keep_b = _add(b, MIX[0], seed=3)
+    tmp = _add(a, MIX[1], seed=4)
+    a.run(1)
+    b.run(1)
+    a.remove(tmp)
+    _add(a, MIX[5], seed=9)
+    a.run(2)
+    b.run(2)
+    Nx, Ny = MIX[0][2], MIX[0][3]
+    assert np.array_equal(a.moments(keep_a, Nx, Ny)[1], b.moments(keep_b, Nx, Ny)[1])
+
+
+def test_autotune_keeps_results_exact():
+    """Autotuning changes launch shapes only: after it, a solve still equals
+    a reference engine advanced by the same number of steps."""
+    import paper_1510_08886_gb300 as lbm
+    a = lbm.Engine("fp32", max_solves=8, arena_bytes=128 << 20, chunk=10)
+    b = lbm.Engine("fp32", max_solves=8, arena_bytes=128 << 20, chunk=10)
+    sa = [_add(a, s, seed=7) for s in MIX[:4]]
+    sb = [_add(b, s, seed=7) for s in MIX[:4]]
+    ms = a.autotune()
+    assert ms > 0
+    steps = a.info(sa[0])[0]
+    assert steps == 30 * 10       # 2 factors x 5 grabs x 3 chunks of 10
+    a.run(1)
+    b.run(steps // 10 + 1)
+    for x, y, spec in zip(sa, sb, MIX[:4]):
+        assert np.array_equal(a.moments(x, spec[2], spec[3])[1], b.moments(y, spec[2], spec[3])[1])
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_16bit_engine_close_to_fp32(precision):
+    import paper_1510_08886_gb300 as lbm
+    e32 = lbm.Engine("fp32", max_solves=4, arena_bytes=64 << 20)
+    e16 = lbm.Engine(precision, max_solves=4, arena_bytes=64 << 20)
+    s32 = _add(e32, MIX[0], seed=2)
+    s16 = _add(e16, MIX[0], seed=2)
+    e32.run(2)
+    e16.run(2)
+    Nx, Ny = MIX[0][2], MIX[0][3]
+    u32 = e32.moments(s32, Nx, Ny)[1]
+    u16 = e16.moments(s16, Nx, Ny)[1]
+    tol = 2e-3 if precision == "fp16" else 2e-2
+    assert np.max(np.abs(u16 - u32)) < tol * np.max(np.abs(u32))
+
+
+def test_config4_workload_runs():
+    """The 256-channel config-4 list (seeded) fits, runs, and every solve
+    stays finite with a positive mass flow."""
+    import paper_1510_08886_gb300 as lbm
+    work = batch_workload(256)
+    need = sum(lbm.Engine.solve_bytes(*lbm.dvm(it["dvm"]), it["Nx"], it["Ny"], "fp32")
+               for it in work)
+    eng = lbm.Engine("fp32", max_solves=256, arena_bytes=need + (64 << 20), chunk=20)
+    slots = []
+    for it in work:
+        e, w, c = lbm.dvm(it["dvm"])
+        s = eng.add(e, w, c, it["order"], it["Nx"], it["Ny"], it["Kn"],
+                    oracle.force_for_mach(it["Kn"]))
+        assert s is not None
+        slots.append(s)
+    res = eng.run(2)
+    for s in slots:
+        assert eng.info(s)[1] == 0
+        assert res[s, 1] > 0 and np.isfinite(res[s, 1])
