@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--kn", type=float, default=0.1)
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=8.0)
     return p.parse_args()
 
 
@@ -165,6 +168,93 @@ def cpu_baseline(precision, Kn):
     return {"value": NX * NY / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"1 time step of the full {NX}x{NY} workload, fp64 C oracle, "
                       f"1 thread ({dt:.1f} s)"}
+
+
+def batched_section(lbm, torch):
+    """Config-4 workload: 256 channels of uneven sizes, D2V33 (N=4) and the
+    D3V107 (x, z) marginal (N=3), fp32, in the engine (persistent kernel per
+    velocity set, CUDA-graph chunks, autotuned) vs the same channels stepped
+    one solve at a time through the single-solve API."""
+    from lbm_inputs import batch_workload
+    work = batch_workload(256)
+    sets = {n: lbm.dvm(n) for n in {it["dvm"] for it in work}}
+    cells = sum(it["Nx"] * it["Ny"] for it in work)
+    need = sum(lbm.Engine.solve_bytes(*sets[it["dvm"]], it["Nx"], it["Ny"], "fp32") for it in work)
+    eng = lbm.Engine("fp32", max_solves=256, arena_bytes=need + (64 << 20), chunk=100)
+    for it in work:
+        e, w, c = sets[it["dvm"]]
+        assert eng.add(e, w, c, it["order"], it["Nx"], it["Ny"], it["Kn"],
+                       lbm.force_for_mach(it["Kn"])) is not None
+    eng.autotune()
+    eng.run(2)
+    torch.cuda.synchronize()
+    chunks = 10
+    t0 = time.perf_counter()
+    eng.run(chunks)
+    dt = time.perf_counter() - t0
+    batched = cells * chunks * eng.chunk / dt / 1e9
+    eng.close()
+    # same channels, one solve at a time (launch per solve per step)
+    solvers = []
+    for it in work:
+        e, w, c = sets[it["dvm"]]
+        solvers.append(lbm.Solver(e, w, c, it["order"], it["Nx"], it["Ny"], it["Kn"],
+                                  lbm.force_for_mach(it["Kn"]), precision="fp32").init())
+    steps = 20
+    for s in solvers:
+        s.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in solvers:
+        s.step(steps)
+    torch.cuda.synchronize()
+    dt1 = time.perf_counter() - t0
+    per_solve = cells * steps / dt1 / 1e9
+    for s in solvers:
+        s.close()
+    return {"workload": "256 channels, seed 20151030: Ny U{16..512}, Nx {1,64,256}, Kn log-U[0.01,1], "
+                        "D2V33 N=4 / D3V107xz N=3, fp32",
+            "cells": cells, "GLUPS_engine": batched, "GLUPS_per_solve_api": per_solve,
+            "speedup": batched / per_solve, "timed_steps": chunks * 100}
+
+
+def serving_section(lbm, seconds):
+    """Config-5 stream (Poisson 200/s, D2V16 N=3, Nx=1, Ny U{16..2048}, Kn
+    log-U[0.01,1], tol in {1e-6,1e-8}) for `seconds` of arrivals, served with
+    continuous batching (fp32 engine) vs the plain fp64 per-solve path."""
+    from lbm_inputs import serving_workload
+    from paper_1510_08886_gb300.serving import ContinuousBatcher, requests_from_workload, serve_plain
+    items = serving_workload(duration_s=seconds)
+    sets = {"D2V16": lbm.dvm("D2V16")}
+    eng = lbm.Engine("fp32", max_solves=1024, arena_bytes=2 << 30, chunk=100)
+    b = ContinuousBatcher(eng, sets)
+    st = b.serve(requests_from_workload(items), realtime=True)
+    eng.close()
+    e, w, c = sets["D2V16"]
+
+    def make(r):
+        return lbm.Solver(e, w, c, r.order, r.Nx, r.Ny, r.Kn, r.force, precision="fp64").init()
+
+    served = {r.rid: r for r in b.done}
+    plain_reqs = requests_from_workload(items)
+    plain = serve_plain(plain_reqs, make, realtime=True, time_limit=max(seconds, 1.0))
+    # accuracy of the served fp32 results against the fp64 path on the requests
+    # both paths finished (the fp64 GPU path matches the oracle to 1e-12)
+    errs = [abs(served[r.rid].mdot / r.mdot - 1) for r in plain_reqs
+            if not math.isnan(r.t_done) and r.rid in served and r.converged]
+    # capacity: the same stream with every request queued at once
+    eng = lbm.Engine("fp32", max_solves=1024, arena_bytes=2 << 30, chunk=100)
+    sat = ContinuousBatcher(eng, sets).serve(requests_from_workload(items), realtime=False)
+    eng.close()
+    return {"stream": f"{len(items)} requests in {seconds:.0f} s (Poisson 200/s, seed 20151031)",
+            "served_fp32_continuous_batching": st.as_dict(),
+            "plain_fp64_per_solve": plain.as_dict(),
+            "solves_per_s_ratio": st.solves_per_s / max(plain.solves_per_s, 1e-12),
+            "served_saturated_solves_per_s": sat.solves_per_s,
+            "saturated_vs_plain": sat.solves_per_s / max(plain.solves_per_s, 1e-12),
+            "mdot_rel_err_fp32_vs_fp64": {"max": max(errs) if errs else None,
+                                          "median": float(np.median(errs)) if errs else None,
+                                          "requests": len(errs)}}
 
 
 def run_reference(args):
@@ -334,6 +424,9 @@ def main():
                     "achieved_GBs": 2 * V * el * ncell * lb / (vms * 1e-3) / 1e9,
                     "mdot": vm, "status": vst})
 
+    batched = None if args.no_batched else batched_section(lbm, torch)
+    serving = None if args.no_serving else serving_section(lbm, args.serve_seconds)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.precision, args.kn)
@@ -364,6 +457,8 @@ def main():
             "clocks": clocks,
             "status": status, "mdot": mdot,
             "variants": variants,
+            "batched": batched,
+            "serving": serving,
         }))
     if dist:
         dist.destroy_process_group()

@@ -337,10 +337,12 @@ class Engine:
         check(_lib.lib().lbm_engine_autotune(self._h, ctypes.byref(ms)), "lbm_engine_autotune")
         return ms.value
 
-    def info(self, slot):
+    def info(self, slot, status=False):
+        """(steps done, status); the status (a device read) only when asked."""
         steps = ctypes.c_long(0)
         st = ctypes.c_int(0)
-        check(_lib.lib().lbm_engine_info(self._h, int(slot), ctypes.byref(steps), ctypes.byref(st)),
+        check(_lib.lib().lbm_engine_info(self._h, int(slot), ctypes.byref(steps),
+                                         ctypes.byref(st) if status else None),
               "lbm_engine_info")
         return steps.value, st.value
 

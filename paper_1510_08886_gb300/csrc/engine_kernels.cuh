@@ -35,7 +35,8 @@ struct EngineTile {
 
 // emit: 0 = nothing, 1 = rho, u_x, u_y into the moment fields, 2 = u_x into prev
 template <class SET, int N, typename S, typename C>
-__global__ void __launch_bounds__(kBlock, min_blocks_for(SET::R + 2 * SET::P + 8, sizeof(C)))
+__global__ void __launch_bounds__(kBlock, min_blocks_for(SET::R + 2 * SET::P + (SET::P > 20 ? 24 : 12),
+                                                         sizeof(C)))
 k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __restrict__ tiles,
               const int* __restrict__ ntiles_p, int* __restrict__ counter,
               const unsigned int* __restrict__ seed_p, int parity, int emit, int chunk) {
@@ -76,11 +77,15 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
             const int x0 = c0 - y0 * k.Nx;
             const bool fast = x0 >= k.maxex && x0 + kBlock - 1 + k.maxex < k.Nx &&
                               y0 >= k.maxey && y0 < k.Ny - k.maxey;
+            const int y1 = (min(c0 + kBlock, k.ncell) - 1) / k.Nx;
+            const bool rows = !fast && y0 >= k.maxey && y1 < k.Ny - k.maxey;
             if (!fast && cell >= k.ncell) continue;
             C f[V];
             if (fast) {
 #pragma unroll
                 for (int a = 0; a < V; ++a) f[a] = ld_pop<S, C>(k, sp[a][cell], a);
+            } else if (rows) {
+                pull_rows<V, S, C>(k, sp, cell, f);
             } else {
                 const int y = cell / k.Nx;
                 const int x = cell - y * k.Nx;

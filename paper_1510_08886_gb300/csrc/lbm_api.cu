@@ -185,6 +185,7 @@ void fill_params_impl(const lbm::SolveSpec* s, KParams<C>& k) {
         k.ey[a] = s->ey[a];
         k.sx[a] = ((s->ex[a] % s->Nx) + s->Nx) % s->Nx;
         k.off[a] = s->ey[a] * s->Nx + s->ex[a];
+        k.dx[a] = s->ex[a] - k.sx[a];
         k.w[a] = s->w[a];
         k.sw[a] = C(s->w[a] * s->scale);
         k.isw[a] = C(1.0 / (s->w[a] * s->scale));

@@ -45,6 +45,7 @@ struct KParams {
     int ex[LBM_MAX_V], ey[LBM_MAX_V];
     int sx[LBM_MAX_V];           // e_x mod Nx, in [0, Nx)
     int off[LBM_MAX_V];          // e_y Nx + e_x: pull offset of an interior node
+    int dx[LBM_MAX_V];           // e_x - sx: offset correction when x - e_x wraps
     // per launch: plane base pointers of the source lattice shifted by the
     // interior pull offset (srcf[a] = src + a plane - off[a]) and of the
     // destination lattice (dstp[a] = dst + a plane)

@@ -320,11 +320,29 @@ __device__ __forceinline__ void relax_ct(const KParams<C>& k, const CellCoef<C>&
                                                          f[SET::R + I], f[SET::R + SET::P + I]), ...);
 }
 
+// Middle path of a tile whose rows all lie at least max|e_y| rows from both
+// walls (the nodes may wrap around x): the source of plane a is
+// cell - off[a] + dx[a] (+ Nx when x - e_x wraps below 0), with
+// sp[a] = lattice + a plane - off[a].
+template <int V, typename S, typename C, typename PTR>
+__device__ __forceinline__ void pull_rows(const KParams<C>& k, const PTR& sp, int cell, C* f) {
+    const int y = cell / k.Nx;
+    const int x = cell - y * k.Nx;
+#pragma unroll
+    for (int a = 0; a < V; ++a) {
+        const int i = cell + k.dx[a] + (x < k.sx[a] ? k.Nx : 0);
+        f[a] = ld_pop<S, C>(k, static_cast<const S*>(sp[a])[i], a);
+    }
+}
+
 // Fused step for a compiled velocity set: the V populations stay in registers
 // between the moment pass and the relaxation pass.
 //  - fast path (block-uniform): the block's nodes lie in one row at least
 //    max|e_y| rows from both walls and max|e_x| columns from both ends, so
 //    every pull is a fixed offset from the node: one address per population;
+//  - rows path (block-uniform): all rows of the block are away from the walls
+//    but nodes may wrap around x (narrow channels, x ends): a compare and a
+//    select per population;
 //  - general path: periodic wrap in x and the diffuse-wall fill near walls.
 template <class SET, int N, typename S, typename C>
 __global__ void __launch_bounds__(kBlock, min_blocks_for(SET::R + 2 * SET::P, sizeof(C)))
@@ -337,10 +355,15 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
     const int x0 = c0 - y0 * k.Nx;
     const bool fast = x0 >= k.maxex && x0 + kBlock - 1 + k.maxex < k.Nx && y0 >= k.maxey &&
                       y0 < k.Ny - k.maxey;
+    const int y1 = (min(c0 + kBlock, k.ncell) - 1) / k.Nx;
+    const bool rows = !fast && y0 >= k.maxey && y1 < k.Ny - k.maxey;
     C f[V];
     if (fast) {
 #pragma unroll
         for (int a = 0; a < V; ++a) f[a] = ld_pop<S, C>(k, static_cast<const S*>(k.srcf[a])[cell], a);
+    } else if (rows) {
+        if (cell >= k.ncell) return;
+        pull_rows<V, S, C>(k, k.srcf, cell, f);
     } else {
         if (cell >= k.ncell) return;
         const int y = cell / k.Nx;

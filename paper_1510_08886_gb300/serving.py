@@ -1,0 +1,194 @@
+"""Serving loop: channel solves arriving over time, run to steady state with
+continuous batching on the multi-solve engine.
+
+Requests (velocity set, Hermite order, Nx, Ny, Kn, tolerance on max|du|) are
+admitted into engine slots as soon as a slot and arena memory are free
+(admission by HBM footprint, first fit over the queue so one large request
+does not block smaller ones); all resident solves advance together one chunk
+at a time; after every chunk each solve whose last step changed u_x by less
+than its tolerance is harvested (mass flow, slip velocity) and its memory
+freed for the queue.  Requests that arrive while others are running join at
+the next chunk boundary.
+
+``serve_plain`` is the comparison path: the same requests solved one at a
+time with the single-solve fp64 API.
+"""
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    t_arrival: float
+    dvm: str
+    order: int
+    Nx: int
+    Ny: int
+    Kn: float
+    tol: float
+    mach: float = 1e-3
+    # filled in by the server
+    t_admit: float = math.nan
+    t_done: float = math.nan
+    steps: int = 0
+    mdot: float = math.nan
+    us: float = math.nan
+    du: float = math.nan
+    converged: bool = False
+    status: int = 0
+
+    @property
+    def force(self):
+        """g = 8 tau Ma (no-slip Navier-Stokes centre speed Ma c0), tau = sqrt(2/pi) Kn."""
+        return 8.0 * math.sqrt(2.0 / math.pi) * self.Kn * self.mach
+
+    @property
+    def latency(self):
+        return self.t_done - self.t_arrival
+
+
+def requests_from_workload(items):
+    return [Request(i, it["t_arrival"], it["dvm"], it["order"], it["Nx"], it["Ny"], it["Kn"],
+                    it["tol"]) for i, it in enumerate(items)]
+
+
+@dataclass
+class ServeStats:
+    completed: int
+    wall_s: float
+    solves_per_s: float
+    p50_s: float
+    p99_s: float
+    mean_queue_s: float
+    max_resident: int
+    chunks: int
+    cell_steps: float
+    extra: dict = field(default_factory=dict)
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k in ("completed", "wall_s", "solves_per_s", "p50_s", "p99_s",
+                                          "mean_queue_s", "max_resident", "chunks", "cell_steps")}
+        d.update(self.extra)
+        return d
+
+
+def _stats(done, t0, t1, max_resident, chunks, cell_steps):
+    lat = np.array([r.latency for r in done]) if done else np.array([math.nan])
+    q = np.array([r.t_admit - r.t_arrival for r in done]) if done else np.array([math.nan])
+    wall = max(t1 - t0, 1e-9)
+    return ServeStats(len(done), wall, len(done) / wall, float(np.percentile(lat, 50)),
+                      float(np.percentile(lat, 99)), float(np.mean(q)), max_resident, chunks,
+                      cell_steps)
+
+
+class ContinuousBatcher:
+    """Drive an engine (paper_1510_08886_gb300.Engine, or any object with
+    add/remove/run/info/chunk) with a request queue."""
+
+    def __init__(self, engine, velocity_sets, max_steps=200000, clock=time.perf_counter):
+        self.engine = engine
+        self.sets = velocity_sets          # name -> (e, w, c)
+        self.max_steps = max_steps
+        self.clock = clock
+        self.queue = []
+        self.active = {}                   # slot -> Request
+        self.done = []
+        self.chunks = 0
+        self.cell_steps = 0.0
+        self.max_resident = 0
+
+    def submit(self, req):
+        self.queue.append(req)
+
+    def admit(self):
+        """First fit over the queue in arrival order."""
+        still = []
+        for r in self.queue:
+            e, w, c = self.sets[r.dvm]
+            slot = self.engine.add(e, w, c, r.order, r.Nx, r.Ny, r.Kn, r.force)
+            if slot is None:
+                still.append(r)
+                continue
+            r.t_admit = self.clock()
+            self.active[slot] = r
+        self.queue = still
+        self.max_resident = max(self.max_resident, len(self.active))
+
+    def step(self):
+        """Admit, advance every resident solve by one chunk, harvest."""
+        self.admit()
+        if not self.active:
+            return 0
+        res = self.engine.run(1)
+        self.chunks += 1
+        self.cell_steps += sum(r.Nx * r.Ny for r in self.active.values()) * self.engine.chunk
+        now = self.clock()
+        finished = []
+        for slot, r in self.active.items():
+            steps, _ = self.engine.info(slot)
+            du = float(res[slot, 0])
+            status = 0 if math.isfinite(du) else -5      # a non-finite state makes du NaN
+            if status != 0 or du < r.tol or steps >= self.max_steps:
+                r.steps, r.status, r.du = steps, status, du
+                r.converged = status == 0 and du < r.tol
+                r.mdot, r.us = float(res[slot, 1]), float(res[slot, 2])
+                r.t_done = now
+                finished.append(slot)
+        for slot in finished:
+            self.engine.remove(slot)
+            self.done.append(self.active.pop(slot))
+        return len(finished)
+
+    def serve(self, requests, realtime=True, time_limit=None):
+        """Play a request stream (t_arrival relative to the start) and return
+        ServeStats.  With realtime=False, arrival times are ignored (every
+        request is queued at once)."""
+        pending = sorted(requests, key=lambda r: r.t_arrival)
+        t0 = self.clock()
+        i = 0
+        while i < len(pending) or self.queue or self.active:
+            now = self.clock()
+            if time_limit is not None and now - t0 > time_limit:
+                break
+            while i < len(pending) and (not realtime or pending[i].t_arrival <= now - t0):
+                r = pending[i]
+                r.t_arrival = t0 + r.t_arrival if realtime else t0
+                self.submit(r)
+                i += 1
+            if not self.queue and not self.active and i < len(pending):
+                time.sleep(max(0.0, min(0.01, pending[i].t_arrival - (self.clock() - t0))))
+                continue
+            self.step()
+        return _stats(self.done, t0, self.clock(), self.max_resident, self.chunks, self.cell_steps)
+
+
+def serve_plain(requests, make_solver, realtime=True, time_limit=None, check_every=100,
+                max_steps=200000, clock=time.perf_counter):
+    """Comparison path: requests solved one at a time in arrival order with
+    the single-solve API (make_solver(request) -> Solver with run_to_steady).
+    Requests still waiting when time_limit expires are not counted."""
+    pending = sorted(requests, key=lambda r: r.t_arrival)
+    t0 = clock()
+    done = []
+    cell_steps = 0.0
+    for r in pending:
+        now = clock()
+        if time_limit is not None and now - t0 > time_limit:
+            break
+        arrival = t0 + r.t_arrival if realtime else t0
+        if realtime and arrival > now:
+            time.sleep(arrival - now)
+        r.t_arrival = arrival
+        r.t_admit = clock()
+        s = make_solver(r)
+        conv, steps, du = s.run_to_steady(r.tol, max_steps, check_every)
+        r.converged, r.steps, r.du = conv, steps, du
+        r.mdot, r.us = s.mass_flow(), s.slip_velocity()
+        r.t_done = clock()
+        cell_steps += r.Nx * r.Ny * steps
+        done.append(r)
+    return _stats(done, t0, clock(), 1, 0, cell_steps)

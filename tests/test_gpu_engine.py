@@ -58,7 +58,7 @@ def test_alone_vs_mix_bitwise_and_vs_single_solver():
         assert np.max(np.abs(ux - m_mix[1])) <= 1e-6 * np.max(np.abs(ux))
         assert np.max(np.abs(r - m_mix[0])) <= 1e-6
         alone.close()
-        assert mix.info(slots[i]) == (100, 0)
+        assert mix.info(slots[i], status=True) == (100, 0)
 
 
 def test_engine_vs_oracle_steady_state():
@@ -174,5 +174,5 @@ def test_config4_workload_runs():
         slots.append(s)
     res = eng.run(2)
     for s in slots:
-        assert eng.info(s)[1] == 0
+        assert eng.info(s, status=True)[1] == 0
         assert res[s, 1] > 0 and np.isfinite(res[s, 1])

@@ -1,0 +1,169 @@
+"""Host logic of the serving loop, with a fake engine on the CPU: admission by
+footprint (first fit), continuous joining at chunk boundaries, harvesting
+at each request's tolerance, statistics.  No GPU."""
+import math
+
+import numpy as np
+
+from lbm_inputs import serving_workload
+from paper_1510_08886_gb300.serving import (ContinuousBatcher, Request, requests_from_workload,
+                                            serve_plain)
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+
+class FakeEngine:
+    """Footprint = Nx*Ny bytes; du after n steps = 1e-3 exp(-n / (10 Ny Kn))."""
+
+    def __init__(self, capacity, slots, chunk=100, clock=None, chunk_time=1e-3):
+        self.capacity, self.chunk, self.clock, self.chunk_time = capacity, chunk, clock, chunk_time
+        self.slots = [None] * slots
+        self.results = np.zeros((slots, 4))
+        self.peak_bytes = 0
+
+    def used(self):
+        return sum(s["bytes"] for s in self.slots if s)
+
+    def add(self, e, w, c, order, Nx, Ny, Kn, force):
+        need = Nx * Ny
+        if self.used() + need > self.capacity:
+            return None
+        for i, s in enumerate(self.slots):
+            if s is None:
+                self.slots[i] = dict(bytes=need, steps=0, Ny=Ny, Kn=Kn, g=force)
+                self.peak_bytes = max(self.peak_bytes, self.used())
+                return i
+        return None
+
+    def remove(self, slot):
+        assert self.slots[slot] is not None
+        self.slots[slot] = None
+
+    def run(self, chunks):
+        for i, s in enumerate(self.slots):
+            if s:
+                s["steps"] += chunks * self.chunk
+                T = 10.0 * s["Ny"] * s["Kn"]
+                self.results[i] = [1e-3 * math.exp(-s["steps"] / T), 1.0 + s["Kn"], 0.5, 1e-3]
+        if self.clock:
+            self.clock.t += chunks * self.chunk_time
+        return self.results
+
+    def info(self, slot):
+        return self.slots[slot]["steps"], 0
+
+
+SETS = {"D2V16": (None, None, None)}
+
+
+def _reqs(specs):
+    return [Request(i, t, "D2V16", 3, 1, ny, kn, tol) for i, (t, ny, kn, tol) in enumerate(specs)]
+
+
+def test_all_requests_complete_at_their_tolerance():
+    clk = FakeClock()
+    eng = FakeEngine(capacity=10_000, slots=8, clock=clk)
+    b = ContinuousBatcher(eng, SETS, clock=clk)
+    reqs = _reqs([(0.0, 64, 0.1, 1e-6), (0.0, 128, 0.5, 1e-8), (0.0, 32, 0.01, 1e-6)])
+    st = b.serve(reqs, realtime=False)
+    assert st.completed == 3
+    for r in b.done:
+        T = 10.0 * r.Ny * r.Kn
+        assert r.converged and 1e-3 * math.exp(-r.steps / T) < r.tol
+        # harvested at the first chunk boundary below tolerance
+        assert 1e-3 * math.exp(-(r.steps - 100) / T) >= r.tol
+        assert r.mdot == 1.0 + r.Kn
+
+
+def test_admission_respects_footprint_and_first_fit():
+    clk = FakeClock()
+    eng = FakeEngine(capacity=1000, slots=16, clock=clk)
+    b = ContinuousBatcher(eng, SETS, clock=clk)
+    # a large request that must wait, then small ones that fit beside the first
+    reqs = _reqs([(0.0, 600, 1.0, 1e-6), (0.0, 900, 1.0, 1e-6), (0.0, 100, 1.0, 1e-6),
+                  (0.0, 200, 1.0, 1e-6)])
+    b.serve(reqs, realtime=False)
+    assert eng.peak_bytes <= 1000
+    order = [r.rid for r in sorted(b.done, key=lambda r: r.t_admit)]
+    assert order.index(2) < order.index(1)       # small request skipped the blocked large one
+    assert all(r.converged for r in b.done)
+
+
+def test_slots_limit_and_queue_wait():
+    clk = FakeClock()
+    eng = FakeEngine(capacity=10**9, slots=2, clock=clk)
+    b = ContinuousBatcher(eng, SETS, clock=clk)
+    reqs = _reqs([(0.0, 64, 0.1, 1e-6)] * 5)
+    st = b.serve(reqs, realtime=False)
+    assert st.completed == 5 and st.max_resident == 2
+    waits = sorted(r.t_admit - r.t_arrival for r in b.done)
+    assert waits[0] == 0.0 and waits[-1] > 0.0
+
+
+def test_requests_join_at_chunk_boundaries_in_realtime():
+    """Requests arriving while others run are admitted at the next chunk."""
+    import time as _time
+
+    eng = FakeEngine(capacity=10**9, slots=32, chunk=100, chunk_time=0.0)
+    real_run = eng.run
+
+    def slow_run(n):
+        _time.sleep(0.002)
+        return real_run(n)
+
+    eng.run = slow_run
+    b = ContinuousBatcher(eng, SETS)
+    reqs = _reqs([(0.0, 400, 1.0, 1e-9), (0.02, 64, 0.1, 1e-6), (0.04, 64, 0.1, 1e-6)])
+    st = b.serve(reqs, realtime=True)
+    assert st.completed == 3
+    first = next(r for r in b.done if r.rid == 0)
+    later = [r for r in b.done if r.rid > 0]
+    assert all(r.t_admit < first.t_done for r in later)   # joined while rid 0 was running
+    assert st.max_resident >= 2
+
+
+def test_stats_percentiles():
+    clk = FakeClock()
+    eng = FakeEngine(capacity=10**9, slots=64, clock=clk)
+    b = ContinuousBatcher(eng, SETS, clock=clk)
+    reqs = _reqs([(0.0, ny, 0.2, 1e-7) for ny in range(16, 80, 4)])
+    st = b.serve(reqs, realtime=False)
+    lat = np.array([r.latency for r in b.done])
+    assert math.isclose(st.p50_s, np.percentile(lat, 50))
+    assert math.isclose(st.p99_s, np.percentile(lat, 99))
+    assert st.solves_per_s > 0 and st.cell_steps > 0
+
+
+def test_serve_plain_sequential():
+    class FakeSolver:
+        def __init__(self, r):
+            self.r = r
+
+        def run_to_steady(self, tol, max_steps, check_every):
+            return True, 500, tol / 2
+
+        def mass_flow(self):
+            return 2.0
+
+        def slip_velocity(self):
+            return 0.3
+
+    reqs = _reqs([(0.0, 64, 0.1, 1e-6), (0.0, 64, 0.2, 1e-6)])
+    st = serve_plain(reqs, FakeSolver, realtime=False)
+    assert st.completed == 2 and all(r.steps == 500 and r.mdot == 2.0 for r in reqs)
+
+
+def test_serving_workload_shape():
+    items = serving_workload(duration_s=5.0)
+    reqs = requests_from_workload(items)
+    assert 700 < len(reqs) < 1300                      # Poisson, mean 200/s
+    assert all(16 <= r.Ny <= 2048 and r.Nx == 1 and r.tol in (1e-6, 1e-8) for r in reqs)
+    assert all(0.01 <= r.Kn <= 1.0 for r in reqs)
+    gaps = np.diff([r.t_arrival for r in reqs])
+    assert 0.003 < gaps.mean() < 0.007
