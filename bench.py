@@ -240,8 +240,9 @@ def serving_section(lbm, seconds):
     plain = serve_plain(plain_reqs, make, realtime=True, time_limit=max(seconds, 1.0))
     # accuracy of the served fp32 results against the fp64 path on the requests
     # both paths finished (the fp64 GPU path matches the oracle to 1e-12)
-    errs = [abs(served[r.rid].mdot / r.mdot - 1) for r in plain_reqs
-            if not math.isnan(r.t_done) and r.rid in served and r.converged]
+    both = [r for r in plain_reqs if not math.isnan(r.t_done) and r.rid in served and r.converged]
+    errs = [abs(served[r.rid].mdot / r.mdot - 1) for r in both]
+    errs_small = [abs(served[r.rid].mdot / r.mdot - 1) for r in both if r.Ny <= 512]
     # capacity: the same stream with every request queued at once
     eng = lbm.Engine("fp32", max_solves=1024, arena_bytes=2 << 30, chunk=100)
     sat = ContinuousBatcher(eng, sets).serve(requests_from_workload(items), realtime=False)
@@ -254,7 +255,9 @@ def serving_section(lbm, seconds):
             "saturated_vs_plain": sat.solves_per_s / max(plain.solves_per_s, 1e-12),
             "mdot_rel_err_fp32_vs_fp64": {"max": max(errs) if errs else None,
                                           "median": float(np.median(errs)) if errs else None,
-                                          "requests": len(errs)}}
+                                          "requests": len(errs),
+                                          "max_Ny_le_512": max(errs_small) if errs_small else None,
+                                          "requests_Ny_le_512": len(errs_small)}}
 
 
 def run_reference(args):
