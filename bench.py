@@ -59,10 +59,8 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1510_08886_gb300 import replicas
+    return replicas.env()
 
 
 def measured_peaks():
@@ -302,10 +300,10 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
     torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1510_08886_gb300 import replicas
+    dist = replicas.init("nccl", torch.device("cuda", local))
+    if ws > 1:      # scaling runs time the headline workload only
+        args.no_variants = args.no_batched = args.no_serving = True
 
     import __graft_entry__
     __graft_entry__.build_library()
@@ -318,7 +316,7 @@ def main():
     ncell = NX * NY
     g = lbm.force_for_mach(args.kn)
     stream = torch.cuda.Stream()
-    rho_host = rho_field(NX, NY, seed=SEED + rank)
+    rho_host = rho_field(NX, NY, seed=replicas.replica_seed(SEED, rank))
     rho_dev = torch.tensor(rho_host, device="cuda")
 
     def barrier():
@@ -354,12 +352,9 @@ def main():
     # ---- headline: device-resident throughput ------------------------------
     ms, clocks, status, mdot = timed_run(args.precision, args.kn, args.lb_steps, args.steps,
                                          args.warmup, sample_clocks=True)
-    ms_t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
     launches = args.steps * args.lb_steps
-    value = ws * ncell * launches / (ms_max * 1e-3) / 1e9
+    value, s_max = replicas.aggregate_rate(ncell * launches / 1e9, ms * 1e-3, dist, "cuda")
+    ms_max = s_max * 1e3
     ELEM = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
     elem = ELEM[args.precision]
     bytes_per_launch = 2 * V * elem * ncell          # read + write every population once
@@ -407,10 +402,8 @@ def main():
     wall = time.perf_counter() - t0
     e2e_ms = wall * 1e3          # host wall clock: copies, launches and reads included
     s.close()
-    e2e_t = torch.tensor([e2e_ms], device="cuda")
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = ws * ncell * args.steps * args.lb_steps / (float(e2e_t.item()) * 1e-3) / 1e9
+    e2e_value, _ = replicas.aggregate_rate(ncell * args.steps * args.lb_steps / 1e9,
+                                           e2e_ms * 1e-3, dist, "cuda")
 
     # ---- variants: both precisions, Kn in {0.01, 0.1, 1.0} -----------------
     variants = []
