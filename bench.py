@@ -241,6 +241,13 @@ def serving_section(lbm, seconds):
     both = [r for r in plain_reqs if not math.isnan(r.t_done) and r.rid in served and r.converged]
     errs = [abs(served[r.rid].mdot / r.mdot - 1) for r in both]
     errs_small = [abs(served[r.rid].mdot / r.mdot - 1) for r in both if r.Ny <= 512]
+    # precision alone: the fp64 path advanced by exactly the served step count
+    same = []
+    for r in both[:40]:
+        sv = served[r.rid]
+        s64 = make(r).step(sv.steps)
+        same.append((r.Ny, abs(sv.mdot / s64.mass_flow() - 1)))
+        s64.close()
     # capacity: the same stream with every request queued at once
     eng = lbm.Engine("fp32", max_solves=1024, arena_bytes=2 << 30, chunk=100)
     sat = ContinuousBatcher(eng, sets).serve(requests_from_workload(items), realtime=False)
@@ -255,7 +262,13 @@ def serving_section(lbm, seconds):
                                           "median": float(np.median(errs)) if errs else None,
                                           "requests": len(errs),
                                           "max_Ny_le_512": max(errs_small) if errs_small else None,
-                                          "requests_Ny_le_512": len(errs_small)}}
+                                          "requests_Ny_le_512": len(errs_small),
+                                          "note": "each path stops at its own tolerance test"},
+            "mdot_rel_err_fp32_vs_fp64_same_steps": {
+                "max": max(e for _, e in same) if same else None,
+                "median": float(np.median([e for _, e in same])) if same else None,
+                "max_Ny_le_512": max([e for n, e in same if n <= 512], default=None),
+                "requests": len(same)}}
 
 
 def run_reference(args):
