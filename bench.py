@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-config1", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=8.0)
     return p.parse_args()
 
@@ -214,6 +215,45 @@ def batched_section(lbm, torch):
                         "D2V33 N=4 / D3V107xz N=3, fp32",
             "cells": cells, "GLUPS_engine": batched, "GLUPS_per_solve_api": per_solve,
             "speedup": batched / per_solve, "timed_steps": chunks * 100}
+
+
+def torch_stream():
+    import torch
+    return torch.cuda.Stream()
+
+
+def config1_section(lbm):
+    """Config 1: D2V16, N=3, Nx=1 x Ny=64, Kn=0.1, Ma 1e-3, rho=1, run until
+    max|du| < 1e-10 tested every 100 steps (<= 50k steps): wall time to steady
+    state on the GPU (fp64 and fp32; launched step by step on the default
+    stream, or as CUDA-graph chunks on a side stream) and with the fp64 CPU
+    oracle."""
+    import oracle
+    Kn = 0.1
+    g = lbm.force_for_mach(Kn)
+    e, w, c = lbm.dvm("D2V16")
+    out = {}
+    side = torch_stream()
+    for prec, stream in (("fp64", None), ("fp32", None), ("fp64_graphs", side),
+                         ("fp32_graphs", side)):
+        s = lbm.Solver(e, w, c, 3, 1, 64, Kn, g, precision=prec.split("_")[0], stream=stream).init()
+        s.run_to_steady(1e-10, 2000)            # warm-up (first launches, clocks)
+        s.init()
+        t0 = time.perf_counter()
+        conv, steps, du = s.run_to_steady(1e-10, 50000)
+        dt = time.perf_counter() - t0
+        out[prec] = {"converged": conv, "steps": steps, "seconds": dt, "steps_per_s": steps / dt,
+                     "mdot": s.mass_flow(), "us": s.slip_velocity()}
+        s.close()
+    ch = oracle.channel("D2V16", 3, 1, 64, Kn, g).init()
+    t0 = time.perf_counter()
+    conv, steps, du = ch.run_to_steady(1e-10, 50000)
+    dt = time.perf_counter() - t0
+    out["oracle_cpu_1thread"] = {"converged": conv, "steps": steps, "seconds": dt,
+                                 "steps_per_s": steps / dt, "mdot": ch.mass_flow()}
+    out["mdot_rel_err_fp64_gpu_vs_oracle"] = abs(out["fp64"]["mdot"] / ch.mass_flow() - 1)
+    out["mdot_rel_err_fp32_gpu_vs_oracle"] = abs(out["fp32"]["mdot"] / ch.mass_flow() - 1)
+    return out
 
 
 def serving_section(lbm, seconds):
@@ -435,6 +475,7 @@ def main():
 
     batched = None if args.no_batched else batched_section(lbm, torch)
     serving = None if args.no_serving else serving_section(lbm, args.serve_seconds)
+    config1 = None if (args.no_config1 or ws > 1) else config1_section(lbm)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -468,6 +509,7 @@ def main():
             "variants": variants,
             "batched": batched,
             "serving": serving,
+            "config1": config1,
         }))
     if dist:
         dist.destroy_process_group()

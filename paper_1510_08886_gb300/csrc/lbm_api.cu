@@ -28,6 +28,9 @@ struct lbm_solver : lbm::SolveSpec {
     long steps = 0;
     KParams<double> k64{};
     KParams<float> k32{};
+    // run_to_steady chunks captured as CUDA graphs, one per starting lattice
+    cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
+    long chunk_K[2] = {0, 0};
 };
 
 namespace lbm {
@@ -429,6 +432,60 @@ int refresh_scale(lbm_solver* s) {
     return LBM_OK;
 }
 
+// Enqueue one convergence chunk: K-1 steps (the last emitting moments), the
+// copy u_x -> prev, one more step, and the fp64 reductions into b.results.
+int enqueue_chunk(lbm_solver* s, long K) {
+    for (long i = 0; i < K - 1; ++i) {
+        const int rc = launch_step(s, i == K - 2);
+        if (rc) return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(s->b.prev_ux, s->b.ux, size_t(s->Nx) * s->Ny * 8,
+                                    cudaMemcpyDeviceToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int rc = launch_step(s, true);
+    if (rc) return rc;
+    const int n = s->Nx * s->Ny;
+    k_reduce_partial<<<lbm::kReduceBlocks, lbm::kReduceThreads, 0, s->stream>>>(
+        s->b.ux, s->b.prev_ux, n, s->b.partial);
+    k_reduce_final<<<1, 256, 0, s->stream>>>(s->b.partial, lbm::kReduceBlocks, s->b.ux, s->Nx,
+                                             s->Ny, s->tau, s->g, s->Kn, s->b.results);
+    return cuda_status(cudaGetLastError());
+}
+
+// One chunk replayed from a CUDA graph (captured on first use for the current
+// lattice parity); the step counter and lattice index advance as if launched.
+int graph_chunk(lbm_solver* s, long K) {
+    const int par = s->cur;
+    if (!s->chunk_exec[par] || s->chunk_K[par] != K) {
+        if (s->chunk_exec[par]) {
+            cudaGraphExecDestroy(s->chunk_exec[par]);
+            s->chunk_exec[par] = nullptr;
+        }
+        const int cur0 = s->cur;
+        const long steps0 = s->steps;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_status(e);
+        const int rc = enqueue_chunk(s, K);
+        e = cudaStreamEndCapture(s->stream, &g);
+        s->cur = cur0;
+        s->steps = steps0;
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return rc ? rc : cuda_status(e);
+        }
+        e = cudaGraphInstantiate(&s->chunk_exec[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_status(e);
+        s->chunk_K[par] = K;
+    }
+    const cudaError_t e = cudaGraphLaunch(s->chunk_exec[par], s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    s->cur = int((par + K) & 1);
+    s->steps += K;
+    return LBM_OK;
+}
+
 int create_common(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, double force,
                   int precision, void* stream, void* workspace, size_t bytes, bool own,
                   lbm_solver** out) {
@@ -552,6 +609,8 @@ int lbm_create_in(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, doub
 
 void lbm_destroy(lbm_solver* s) {
     if (!s) return;
+    for (auto& g : s->chunk_exec)
+        if (g) cudaGraphExecDestroy(g);
     if (s->owns && s->ws) {
         cudaStreamSynchronize(s->stream);
         cudaFree(s->ws);
@@ -592,15 +651,25 @@ int lbm_run_to_steady(lbm_solver* s, double tol, long max_steps, long check_ever
     if (!s || !(tol > 0) || max_steps < 0 || check_every < 2) return LBM_EINVAL;
     double du = HUGE_VAL;
     int rc = LBM_ENOTCONV;
+    // on a capturable stream, fp32/fp64 chunks replay a CUDA graph
+    const bool graphs = s->stream != nullptr && !is16(s->precision);
     while (s->steps < max_steps) {
         const long n = std::min(check_every, max_steps - s->steps);
-        if (n > 1 && (rc = lbm_step(s, n - 1))) break;
-        cudaError_t e = cudaMemcpyAsync(s->b.prev_ux, s->b.ux, size_t(s->Nx) * s->Ny * 8,
-                                        cudaMemcpyDeviceToDevice, s->stream);
-        if (e != cudaSuccess) { rc = cuda_status(e); break; }
-        if ((rc = lbm_step(s, 1))) break;
         double r[4];
-        if ((rc = reduce(s, true, r))) break;
+        if (graphs) {
+            if ((rc = graph_chunk(s, n))) break;
+            cudaError_t e = cudaMemcpyAsync(r, s->b.results, 4 * sizeof(double),
+                                            cudaMemcpyDeviceToHost, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+            if (e != cudaSuccess) { rc = cuda_status(e); break; }
+        } else {
+            if (n > 1 && (rc = lbm_step(s, n - 1))) break;
+            cudaError_t e = cudaMemcpyAsync(s->b.prev_ux, s->b.ux, size_t(s->Nx) * s->Ny * 8,
+                                            cudaMemcpyDeviceToDevice, s->stream);
+            if (e != cudaSuccess) { rc = cuda_status(e); break; }
+            if ((rc = lbm_step(s, 1))) break;
+            if ((rc = reduce(s, true, r))) break;
+        }
         du = r[1];
         if ((rc = read_status(s))) break;
         if ((rc = refresh_scale(s))) break;

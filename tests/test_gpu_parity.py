@@ -253,3 +253,28 @@ def test_stream_argument_is_used():
     a = lbm.Solver(e, w, c, 3, 4, 16, 0.1, 1e-3, stream=st).init().step(20)
     b = lbm.Solver(e, w, c, 3, 4, 16, 0.1, 1e-3).init().step(20)
     assert np.array_equal(a.populations(), b.populations())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_chunks_equal_launched_steps(precision):
+    """On a non-default stream lbm_run_to_steady replays CUDA-graph chunks;
+    the result is bit-identical to the step-by-step launches of the default
+    stream (same kernels, same arguments), including odd chunk lengths."""
+    import paper_1510_08886_gb300 as lbm
+    e, w, c = lbm.dvm("D2V16")
+    Kn = 0.1
+    g = oracle.force_for_mach(Kn)
+    a = lbm.Solver(e, w, c, 3, 1, 64, Kn, g, precision=precision).init()
+    b = lbm.Solver(e, w, c, 3, 1, 64, Kn, g, precision=precision,
+                   stream=torch.cuda.Stream()).init()
+    ra = a.run_to_steady(1e-10, 50000)
+    rb = b.run_to_steady(1e-10, 50000)
+    assert ra == rb
+    assert np.array_equal(a.populations(), b.populations())
+    assert a.mass_flow() == b.mass_flow()
+    a.step(3)
+    b.step(3)                                  # odd number of steps: other lattice parity
+    ra = a.run_to_steady(1e-14, a.steps + 351, check_every=50)
+    rb = b.run_to_steady(1e-14, b.steps + 351, check_every=50)
+    assert ra == rb
+    assert np.array_equal(a.populations(), b.populations())
