@@ -166,6 +166,14 @@ int lbm_mass_flow(lbm_solver* s, double* mdot, double* mean_ux);
  * Needs Ny >= 4. */
 int lbm_slip_velocity(lbm_solver* s, double* us);
 
+/* Knudsen-layer diagnostic (Eq. uNS, uNEQ): u_neq(y) = u(y) - u_NS(y) for the
+ * x-averaged velocity u(y) of the current state, u_NS the parabola through the
+ * centre value u(0) (as in lbm_slip_velocity) with the same mass flow:
+ * u_NS(y) = u(0) (1 - 3 (1 - <u>/u(0)) (2 z)^2), z = (y + 1/2)/Ny - 1/2, <u>
+ * the mean over all nodes.  uneq: Ny doubles (host).  Needs Ny >= 4.  Uses the
+ * solver's convergence-reference field as scratch. */
+int lbm_knudsen_layer(lbm_solver* s, double* uneq);
+
 /* Device status word: LBM_OK, or LBM_ENONFINITE once any step met a
  * non-finite or non-positive density.  Synchronises the stream. */
 int lbm_status(lbm_solver* s);

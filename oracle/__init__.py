@@ -163,6 +163,30 @@ class Channel:
             uc = np.mean((9.0 * (u[m - 1] + u[m]) - (u[m - 2] + u[m + 1])) / 16.0)
         return float(uw / uc)
 
+    def centre_velocity(self, u=None):
+        """u(0): x-averaged u_x at the channel centre (centre node for odd Ny,
+        four-point midpoint interpolation for even Ny), as for u_s."""
+        u = self.moments()[1] if u is None else u
+        Ny = self.Ny
+        if Ny % 2:
+            return float(np.mean(u[(Ny - 1) // 2]))
+        m = Ny // 2
+        return float(np.mean((9.0 * (u[m - 1] + u[m]) - (u[m - 2] + u[m + 1])) / 16.0))
+
+    def knudsen_layer(self):
+        """Non-equilibrium velocity profile u^(neq)(z) = u(z) - u^(NS)(z)
+        (Eq. uNEQ), u^(NS) the parabola through u(0) with the same mass flow
+        (Eq. uNS): u^(NS)(z) = u(0) (1 - 3 (1 - <u>/u(0)) (z/(l0/2))^2),
+        <u> the mean over the nodes (the integral of Eq. uNS by the midpoint
+        rule), z_j = (j + 1/2)/Ny - 1/2.  Returns an array of Ny values
+        (u averaged over x)."""
+        u = self.moments()[1]
+        uc = self.centre_velocity(u)
+        prof = np.mean(u, axis=1)
+        z = (np.arange(self.Ny) + 0.5) / self.Ny - 0.5
+        uns = uc * (1.0 - 3.0 * (1.0 - np.mean(u) / uc) * (z / 0.5) ** 2)
+        return prof - uns
+
     def run_to_steady(self, tol, max_steps, check_every=100):
         """Step until max |u_x(t) - u_x(t - dt)| < tol, tested every
         ``check_every`` steps.  Returns (converged, steps, last_du)."""

@@ -226,6 +226,12 @@ class Solver:
         check(_lib.lib().lbm_slip_velocity(self._h, ctypes.byref(u)), "lbm_slip_velocity")
         return u.value
 
+    def knudsen_layer(self):
+        """u_neq(y) = u(y) - u_NS(y) (Eq. uNEQ), Ny values."""
+        out = np.empty(self.Ny)
+        check(_lib.lib().lbm_knudsen_layer(self._h, _dp(out)), "lbm_knudsen_layer")
+        return out
+
     def status(self):
         return _lib.lib().lbm_status(self._h)
 

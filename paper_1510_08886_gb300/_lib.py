@@ -50,6 +50,7 @@ SIGNATURES = {
     "lbm_mass_flow": (ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p]),
     "lbm_slip_velocity": (ctypes.c_int, [ctypes.c_void_p, c_double_p]),
     "lbm_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "lbm_knudsen_layer": (ctypes.c_int, [ctypes.c_void_p, c_double_p]),
     "lbm_steps_done": (ctypes.c_int, [ctypes.c_void_p, c_long_p]),
     "lbm_populations": (ctypes.c_int, [ctypes.c_void_p, c_double_p]),
     "lbm_state_bytes": (ctypes.c_int, [ctypes.c_void_p, c_size_p]),

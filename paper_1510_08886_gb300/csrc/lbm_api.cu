@@ -340,6 +340,38 @@ void set_plane_pointers(const lbm_solver* s, KParams<C>& k, const void* src, voi
     }
 }
 
+// Knudsen-layer diagnostic (Eq. uNS, uNEQ), one block: x-averaged u_x per row,
+// u(0) as for the slip velocity, <u> over all nodes, then
+// out[y] = u(y) - u(0) (1 - 3 (1 - <u>/u(0)) (2 z_y)^2), z_y = (y + 1/2)/Ny - 1/2.
+__global__ void __launch_bounds__(256)
+k_knudsen_layer(const double* __restrict__ ux, int Nx, int Ny, double* __restrict__ out) {
+    __shared__ double sh[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int y = warp; y < Ny; y += 8) {
+        double v = 0.0;
+        for (int x = lane; x < Nx; x += 32) v += ux[(long long)y * Nx + x];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) out[y] = v / Nx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mean = 0.0;
+        for (int y = 0; y < Ny; ++y) mean += out[y];
+        mean /= Ny;
+        const int m = Ny / 2;
+        const double uc = (Ny & 1) ? out[(Ny - 1) / 2]
+                                   : (9.0 * (out[m - 1] + out[m]) - (out[m - 2] + out[m + 1])) / 16.0;
+        sh[0] = uc;
+        sh[1] = 3.0 * (1.0 - mean / uc);
+    }
+    __syncthreads();
+    const double uc = sh[0], a = sh[1];
+    for (int y = threadIdx.x; y < Ny; y += blockDim.x) {
+        const double z2 = 2.0 * ((y + 0.5) / Ny - 0.5);
+        out[y] -= uc * (1.0 - a * z2 * z2);
+    }
+}
+
 int launch_step(lbm_solver* s, bool emit) {
     const void* src = static_cast<const char*>(s->b.f[s->cur]);
     void* dst = s->b.f[1 - s->cur];
@@ -710,6 +742,17 @@ int lbm_slip_velocity(lbm_solver* s, double* us) {
     int rc = reduce(s, false, r);
     if (rc) return rc;
     *us = r[2];
+    return read_status(s);
+}
+
+int lbm_knudsen_layer(lbm_solver* s, double* uneq) {
+    if (!s || !uneq || s->Ny < 4) return LBM_EINVAL;
+    k_knudsen_layer<<<1, 256, 0, s->stream>>>(s->b.ux, s->Nx, s->Ny, s->b.prev_ux);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(uneq, s->b.prev_ux, size_t(s->Ny) * 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
     return read_status(s);
 }
 

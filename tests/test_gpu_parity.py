@@ -278,3 +278,35 @@ def test_graph_chunks_equal_launched_steps(precision):
     rb = b.run_to_steady(1e-14, b.steps + 351, check_every=50)
     assert ra == rb
     assert np.array_equal(a.populations(), b.populations())
+
+
+@pytest.mark.parametrize("name", ["D3V96xz", "D2V16"])
+def test_knudsen_layer_parity(name):
+    """u_neq(y) (Eq. uNEQ) from the GPU state against the oracle's, fp64."""
+    Kn = 0.05
+    g = oracle.force_for_mach(Kn)
+    s, ref, _ = _pair(name, 3, 2, 96, Kn, g, None)
+    s.run_to_steady(1e-11, 200000)
+    ref.run_to_steady(1e-11, 200000)
+    un_g = s.knudsen_layer()
+    un_o = ref.knudsen_layer()
+    uc = ref.centre_velocity()
+    assert np.max(np.abs(un_g - un_o)) < 1e-11 * uc
+
+
+def test_knudsen_minimum_s3_not_s4_on_gpu():
+    """Sect. VI.B/C on the GPU engine (fp32): the S3 marginal has its mass-flow
+    minimum between Kn 0.7 and 1.4, the S4 marginal none up to Kn 3."""
+    import paper_1510_08886_gb300 as lbm
+    kns = [0.45, 0.7, 1.0, 1.4, 2.0, 3.0]
+    eng = lbm.Engine("fp32", max_solves=16, arena_bytes=32 << 20)
+    slots = {}
+    for name in ("D3V107xz", "D3V96xz"):
+        e, w, c = lbm.dvm(name)
+        for Kn in kns:
+            slots[(name, Kn)] = eng.add(e, w, c, 3, 1, 48, Kn, oracle.force_for_mach(Kn))
+    res = eng.run(60)
+    s3 = np.array([res[slots[("D3V107xz", k)], 1] for k in kns])
+    s4 = np.array([res[slots[("D3V96xz", k)], 1] for k in kns])
+    assert 1 <= int(np.argmin(s3)) <= 3 and s3[-1] > 1.05 * s3.min()
+    assert np.all(np.diff(s4) < 0)

@@ -339,3 +339,58 @@ def test_fixed_point_by_newton_on_tiny_grid():
         x = x - np.linalg.solve(J, r)
     newton = ch2.moments(x.reshape(ch2.f.shape))[1][:, 0]
     assert np.max(np.abs(newton - marched)) < 1e-9 * np.max(np.abs(marched))
+
+
+def test_knudsen_layer_mean_closed_form():
+    """Eq. uNS with the midpoint rule: (1/Ny) sum_j (2 z_j)^2 = (Ny^2 - 1)/(3 Ny^2),
+    so the node mean of u_neq is exactly -(u(0) - <u>)/Ny^2."""
+    Kn = 0.1
+    ch = oracle.channel("D2V16", 3, 2, 40, Kn, oracle.force_for_mach(Kn)).init()
+    ch.run_to_steady(1e-11, 50000)
+    un = ch.knudsen_layer()
+    uc = ch.centre_velocity()
+    assert abs(np.mean(un) + (uc - ch.mean_ux()) / 40 ** 2) < 1e-15
+    assert np.max(np.abs(un - un[::-1])) < 1e-12 * uc
+
+
+def test_knudsen_layer_hierarchy():
+    """Sect. VI.D: a quadrature of order 5 gives a quadratic profile (u_neq ~ 0,
+    here up to discretisation); the scattering S4 model shows a velocity defect at
+    the wall (u_neq < 0) of a few per cent at Kn = 0.05."""
+    from numpy import sqrt
+    t = dict(D=2, V=9, c=sqrt(3.0), groups=[((0, 0), 1, 4 / 9), ((1, 0), 4, 1 / 9),
+                                            ((1, 1), 4, 1 / 36)])
+    e9, w9, c9 = dvm.expand(t)
+    Kn = 0.05
+    g = oracle.force_for_mach(Kn)
+    q5 = oracle.Channel(e9, w9, c9, 2, 1, 96, Kn, g).init()
+    q5.run_to_steady(1e-11, 200000)
+    s4 = oracle.channel("D3V96xz", 3, 1, 96, Kn, g).init()
+    s4.run_to_steady(1e-11, 200000)
+    r5 = np.max(np.abs(q5.knudsen_layer())) / q5.centre_velocity()
+    u4 = s4.knudsen_layer() / s4.centre_velocity()
+    assert r5 < 2e-4
+    assert u4[0] < -1e-2 and u4[-1] < -1e-2
+    assert np.max(np.abs(u4)) > 50 * r5
+
+
+@pytest.mark.slow
+def test_knudsen_minimum_s3_not_s4():
+    """Sect. VI.B/C: the wall-exact S3 model (sigma_zxx = 0) reproduces the
+    Knudsen minimum of the mass flow near Kn = 1; the scattering S4 model has
+    none (mdot keeps decreasing).  (x, z) marginals, Ny = 48."""
+    kns = [0.45, 0.7, 1.0, 1.4, 2.0, 3.0]
+
+    def sweep(name):
+        out = []
+        for Kn in kns:
+            ch = oracle.channel(name, 3, 1, 48, Kn, oracle.force_for_mach(Kn)).init()
+            ch.run_to_steady(1e-10, 100000)
+            out.append(ch.mass_flow())
+        return np.array(out)
+
+    s3 = sweep("D3V107xz")
+    s4 = sweep("D3V96xz")
+    assert 1 <= int(np.argmin(s3)) <= 3           # minimum between Kn 0.7 and 1.4
+    assert s3[-1] > s3.min() * 1.05
+    assert np.all(np.diff(s4) < 0)
