@@ -77,12 +77,15 @@ class ServeStats:
 
 
 def _stats(done, t0, t1, max_resident, chunks, cell_steps):
-    lat = np.array([r.latency for r in done]) if done else np.array([math.nan])
-    q = np.array([r.t_admit - r.t_arrival for r in done]) if done else np.array([math.nan])
+    ok = [r for r in done if r.status == 0]
+    lat = np.array([r.latency for r in ok]) if ok else np.array([math.nan])
+    q = np.array([r.t_admit - r.t_arrival for r in ok]) if ok else np.array([math.nan])
     wall = max(t1 - t0, 1e-9)
-    return ServeStats(len(done), wall, len(done) / wall, float(np.percentile(lat, 50)),
-                      float(np.percentile(lat, 99)), float(np.mean(q)), max_resident, chunks,
-                      cell_steps)
+    st = ServeStats(len(ok), wall, len(ok) / wall, float(np.percentile(lat, 50)),
+                    float(np.percentile(lat, 99)), float(np.mean(q)), max_resident, chunks,
+                    cell_steps)
+    st.extra["failed"] = len(done) - len(ok)
+    return st
 
 
 class ContinuousBatcher:
@@ -105,11 +108,19 @@ class ContinuousBatcher:
         self.queue.append(req)
 
     def admit(self):
-        """First fit over the queue in arrival order."""
+        """First fit over the queue in arrival order.  A request the engine
+        rejects (unknown velocity set, invalid arguments) is answered at once
+        with its error code instead of stopping the server."""
         still = []
         for r in self.queue:
-            e, w, c = self.sets[r.dvm]
-            slot = self.engine.add(e, w, c, r.order, r.Nx, r.Ny, r.Kn, r.force)
+            try:
+                e, w, c = self.sets[r.dvm]
+                slot = self.engine.add(e, w, c, r.order, r.Nx, r.Ny, r.Kn, r.force)
+            except (KeyError, ValueError, RuntimeError) as err:
+                r.status = getattr(err, "code", -1)
+                r.t_admit = r.t_done = self.clock()
+                self.done.append(r)
+                continue
             if slot is None:
                 still.append(r)
                 continue

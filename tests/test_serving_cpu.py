@@ -167,3 +167,38 @@ def test_serving_workload_shape():
     assert all(0.01 <= r.Kn <= 1.0 for r in reqs)
     gaps = np.diff([r.t_arrival for r in reqs])
     assert 0.003 < gaps.mean() < 0.007
+
+
+def test_failures_do_not_stop_the_server():
+    """A request with an unknown velocity set, one the engine rejects, and a
+    solve whose state turns non-finite are answered with an error status while
+    the other requests complete."""
+    clk = FakeClock()
+
+    class Faulty(FakeEngine):
+        def add(self, e, w, c, order, Nx, Ny, Kn, force):
+            if Ny == 13:
+                err = RuntimeError("lbm_engine_add: invalid argument (-1)")
+                err.code = -1
+                raise err
+            return super().add(e, w, c, order, Nx, Ny, Kn, force)
+
+        def run(self, chunks):
+            res = super().run(chunks)
+            for i, s in enumerate(self.slots):
+                if s and s["Ny"] == 17:
+                    res[i, 0] = math.nan        # a NaN in the state makes du NaN
+            return res
+
+    eng = Faulty(capacity=10**9, slots=8, clock=clk)
+    b = ContinuousBatcher(eng, SETS, clock=clk)
+    reqs = _reqs([(0.0, 64, 0.1, 1e-6), (0.0, 13, 0.1, 1e-6), (0.0, 17, 0.1, 1e-6),
+                  (0.0, 32, 0.2, 1e-6)])
+    reqs.append(Request(4, 0.0, "NOPE", 3, 1, 32, 0.1, 1e-6))
+    st = b.serve(reqs, realtime=False)
+    by = {r.rid: r for r in b.done}
+    assert by[0].converged and by[3].converged
+    assert by[1].status == -1 and by[4].status == -1
+    assert by[2].status == -5 and not by[2].converged
+    assert st.completed == 2 and st.extra["failed"] == 3
+    assert all(s is None for s in eng.slots)          # every slot released
