@@ -397,6 +397,85 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
     flag_density<C>(q, b.status);
 }
 
+// Step for tiny channels: LP lanes (a power of 2 >= P) cooperate on one node,
+// lane p holding the pair (R + p, R + P + p); the moments are summed over the
+// node's lanes by butterfly shuffles, every lane derives the node's
+// coefficients, and lane 0 also carries the rest population.  One warp per
+// block, so a channel of a few hundred nodes spreads over many SMs instead of
+// running on one (the fp64 step of a 64-node channel is otherwise bound by a
+// single SM's fp64 lanes).
+template <int LP, int N, typename S, typename C>
+__global__ void __launch_bounds__(32)
+k_step_warp(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __restrict__ dst,
+            const DevBufs b) {
+    constexpr int G = 32 / LP;                 // nodes per warp
+    const int lane = threadIdx.x;
+    const int cell = blockIdx.x * G + lane / LP;
+    const int p = lane % LP;
+    const bool node = cell < k.ncell;
+    const bool act = node && p < k.P;
+    int y = 0, x = 0;
+    if (node) {
+        y = cell / k.Nx;
+        x = cell - y * k.Nx;
+    }
+    const double pb = (node && y < k.maxey) ? wall_dpsi<S, C>(k, src, x, true) : 0.0;
+    const double pt = (node && y >= k.Ny - k.maxey) ? wall_dpsi<S, C>(k, src, x, false) : 0.0;
+    auto value = [&](int a) -> C {
+        const int ys = y - k.ey[a];
+        if (ys < 0) return C(pb * k.w[a]);
+        if (ys >= k.Ny) return C(pt * k.w[a]);
+        return pull<S, C>(k, src, a, x, y);
+    };
+    C fp = C(0), fm = C(0), f0 = C(0);
+    if (act) {
+        fp = value(k.R + p);
+        fm = value(k.R + k.P + p);
+    }
+    if (node && p == 0 && k.R) f0 = value(0);
+    const C sum = fp + fm, dif = fp - fm;
+    const int pp = act ? p : 0;
+    C m[6] = {sum + f0, act ? k.pex[pp] * dif : C(0), act ? k.pey[pp] * dif : C(0),
+              act ? k.pexx[pp] * sum : C(0), act ? k.pexy2[pp] * sum : C(0),
+              act ? k.peyy[pp] * sum : C(0)};
+#pragma unroll
+    for (int o = LP / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) m[i] += __shfl_xor_sync(0xffffffffu, m[i], o);
+    if (!node) return;
+    const CellCoef<C> q = cell_coef<N, C>(k, m[0], m[1], m[2], m[3], C(0.5) * m[4], m[5]);
+    unsigned rs = sr_seed<S, C>(k.seed, cell);
+    if (act) {
+        if (k.force)
+            pair_update<true, C>(k, q, p, fp, fm);
+        else
+            pair_update<false, C>(k, q, p, fp, fm);
+        dst[(long long)(k.R + p) * k.plane + cell] = st_pop<S, C>(k, fp, k.R + p, rs);
+        dst[(long long)(k.R + k.P + p) * k.plane + cell] = st_pop<S, C>(k, fm, k.R + k.P + p, rs);
+    }
+    if (p == 0) {
+        if (k.R) dst[cell] = st_pop<S, C>(k, fma(k.one_m_omega, f0, k.omw_rest * q.a0), 0, rs);
+        emit_moments<C>(k, q, cell, b);
+        flag_density<C>(q, b.status);
+    }
+}
+
+// lanes per node of the tiny-channel kernel for P pairs (0: not used, P > 32)
+inline int warp_lanes(int P) { return P <= 8 ? 8 : (P <= 16 ? 16 : (P <= 32 ? 32 : 0)); }
+
+template <int N, typename S, typename C>
+cudaError_t launch_warp(const KParams<C>& k, int LP, const S* src, S* dst, const DevBufs& b,
+                        cudaStream_t st) {
+    const int G = 32 / LP;
+    const dim3 g((k.ncell + G - 1) / G);
+    switch (LP) {
+        case 8: k_step_warp<8, N, S, C><<<g, 32, 0, st>>>(k, src, dst, b); break;
+        case 16: k_step_warp<16, N, S, C><<<g, 32, 0, st>>>(k, src, dst, b); break;
+        default: k_step_warp<32, N, S, C><<<g, 32, 0, st>>>(k, src, dst, b); break;
+    }
+    return cudaGetLastError();
+}
+
 // Same step for any V <= LBM_MAX_V (R, P at run time).  The populations are
 // read twice (moment pass, relaxation pass); the second read hits L1/L2.
 // INIT = true builds the state from a density field instead of streaming:
@@ -462,6 +541,13 @@ template <int N, typename S, typename C>
 cudaError_t launch_step_n(const KParams<C>& k, const S* src, S* dst, const DevBufs& b,
                           cudaStream_t st) {
     const dim3 g = grid_for(k);
+    // fp64 channels too small to fill the GPU with one node per thread: several
+    // lanes per node (k_step_warp) spread the fp64 work over more SMs
+    if (sizeof(C) == 8) {
+        const int LP = warp_lanes(k.P);
+        if (LP && (long long)k.ncell * LP <= 152ll * 32 * 8)
+            return launch_warp<N, S, C>(k, LP, src, dst, b, st);
+    }
     switch (k.set_id) {
         case 0: k_step_ct<SetD2V16, N, S, C><<<g, kBlock, 0, st>>>(k, src, dst, b); break;
         case 1: k_step_ct<SetD2V32, N, S, C><<<g, kBlock, 0, st>>>(k, src, dst, b); break;

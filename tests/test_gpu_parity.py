@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 # (DVM, Hermite order): every register-resident shape plus generic-kernel sets
 CASES = [("D2V16", 3), ("D2V33", 4), ("D2V32", 3), ("D3V107xz", 3), ("D3V96xz", 3),
          ("D3V112xz", 3), ("D3V77xz", 3), ("D3V66xz", 3), ("D3V59xz", 3), ("D2V33", 3),
-         ("D2V16", 4), ("D2V16", 2)]
+         ("D2V16", 4), ("D2V16", 2), ("D2Q9", 2), ("D2Q9", 3)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -31,11 +31,16 @@ def _built():
     __graft_entry__.build_library()
 
 
+def _tables():
+    from lbm_inputs import TEXTBOOK_TABLES
+    return {**DVM_TABLES, **TEXTBOOK_TABLES}
+
+
 def _pair(name, N, Nx, Ny, Kn, g, rho, precision="fp64"):
     import paper_1510_08886_gb300 as lbm
-    e, w, c = lbm.dvm(name)
+    e, w, c = lbm.dvm(name, _tables())
     s = lbm.Solver(e, w, c, N, Nx, Ny, Kn, g, precision=precision).init(rho)
-    ref = oracle.channel(name, N, Nx, Ny, Kn, g).init(rho)
+    ref = oracle.channel(name, N, Nx, Ny, Kn, g, tables=_tables()).init(rho)
     return s, ref, e
 
 
@@ -55,7 +60,7 @@ def test_fp64_parity_after_steps(name, N, Nx, Ny):
     """Moments and every post-collision population after 60 steps, seeded
     density perturbation, body force on; sizes span several 256-thread
     blocks with a ragged tail, Nx = 1 and Nx < max |e_x| (multiple wraps)."""
-    e, _, _ = __import__("paper_1510_08886_gb300").dvm(name)
+    e, _, _ = __import__("paper_1510_08886_gb300").dvm(name, _tables())
     Ny = max(Ny, int(np.max(np.abs(e[:, 1]))))
     Kn = 0.2
     g = oracle.force_for_mach(Kn, 1e-2)
