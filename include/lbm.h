@@ -228,11 +228,14 @@ void lbm_engine_destroy(lbm_engine* e);
 /* Admit a solve (arguments as lbm_create; rho_host as lbm_init) and
  * initialise it.  *slot receives its slot index.  LBM_ENOMEM when no slot is
  * free or its footprint does not fit in the arena (the caller may retry after
- * a removal).  Synchronises the stream. */
+ * a removal).  Asynchronous on the engine's stream (rho_host is copied before
+ * the call returns); errors of the queued work surface at the next
+ * lbm_engine_run. */
 int lbm_engine_add(lbm_engine* e, const lbm_dvm* dvm, int order, int Nx, int Ny,
                    double Kn, double force, const double* rho_host, int* slot);
 
-/* Release a slot and its arena memory. */
+/* Release a slot and its arena memory.  Stream-ordered: work already queued
+ * for the slot completes before a later solve can use its memory. */
 int lbm_engine_remove(lbm_engine* e, int slot);
 
 /* Steps per chunk, even, 2..1000 (default 100). */

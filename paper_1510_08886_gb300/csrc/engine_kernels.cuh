@@ -84,8 +84,9 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
             if (fast) {
 #pragma unroll
                 for (int a = 0; a < V; ++a) f[a] = ld_pop<S, C>(k, sp[a][cell], a);
-            } else if (rows) {
-                pull_rows<V, S, C>(k, sp, cell, f);
+            } else if (rows || (cell / k.Nx >= k.maxey && cell / k.Nx < k.Ny - k.maxey)) {
+                // nodes away from the walls (the whole tile, or this node of a wall tile)
+                pull_rows_any<SET, S, C>(k, sp, cell, f);
             } else {
                 const int y = cell / k.Nx;
                 const int x = cell - y * k.Nx;

@@ -102,6 +102,11 @@ struct EngSlot {
     int group = -1;
 };
 
+__global__ void k_fill_ones(double* p, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 1.0;
+}
+
 int cuda_rc(cudaError_t e) {
     return e == cudaSuccess ? LBM_OK : (e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA);
 }
@@ -178,7 +183,6 @@ int rebuild_tiles(lbm_engine* e) {
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(e->d_ntiles, counts.data(), kGroups * sizeof(int),
                               cudaMemcpyHostToDevice, e->stream);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
     if (err != cudaSuccess) return cuda_rc(err);
     if (groups != e->groups) e->graph_dirty = true;
     e->groups = groups;
@@ -402,10 +406,8 @@ int lbm_engine_add(lbm_engine* e, const lbm_dvm* dvm, int order, int Nx, int Ny,
         if (rho_host) {
             err = cudaMemcpyAsync(h.prev, rho_host, size_t(n) * 8, cudaMemcpyHostToDevice, e->stream);
         } else {
-            std::vector<double> ones(n, 1.0);
-            err = cudaMemcpyAsync(h.prev, ones.data(), size_t(n) * 8, cudaMemcpyHostToDevice,
-                                  e->stream);
-            if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+            k_fill_ones<<<(n + 255) / 256, 256, 0, e->stream>>>(h.prev, n);
+            err = cudaGetLastError();
         }
     }
     if (err == cudaSuccess) {
@@ -421,7 +423,6 @@ int lbm_engine_add(lbm_engine* e, const lbm_dvm* dvm, int order, int Nx, int Ny,
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(e->d_active + slot, &e->h_active[slot], sizeof(int),
                               cudaMemcpyHostToDevice, e->stream);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
     if (err != cudaSuccess) {
         e->h_active[slot] = 0;
         sl.used = false;
@@ -437,9 +438,10 @@ int lbm_engine_remove(lbm_engine* e, int slot) {
     if (!e || slot < 0 || slot >= e->max_slots || !e->slots[slot].used) return LBM_EINVAL;
     EngSlot& sl = e->slots[slot];
     e->h_active[slot] = 0;
+    // stream-ordered: work already queued for this slot finishes before any
+    // later use of its memory (a new solve's set-up goes on the same stream)
     cudaError_t err = cudaMemcpyAsync(e->d_active + slot, &e->h_active[slot], sizeof(int),
                                       cudaMemcpyHostToDevice, e->stream);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
     if (err != cudaSuccess) return cuda_rc(err);
     e->arena.release(sl.off, sl.bytes);
     sl.used = false;

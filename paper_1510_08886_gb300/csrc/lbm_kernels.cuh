@@ -335,6 +335,59 @@ __device__ __forceinline__ void pull_rows(const KParams<C>& k, const PTR& sp, in
     }
 }
 
+// e_x of plane a of a compiled set (rest, the P pair members, their negatives)
+template <class SET>
+__host__ __device__ constexpr int plane_ex(int a) {
+    return a < SET::R ? 0 : (a < SET::R + SET::P ? SET::ex[a - SET::R] : -SET::ex[a - SET::R - SET::P]);
+}
+
+// Rows path with e_x known at compile time (all rows of the node away from the
+// walls).  sp[a] = lattice + a plane - (e_y Nx + e_x) (a pointer, or for the
+// single-solve kernel a byte address).  With Nx >= max|e_x|
+// the x wrap is one compare against a constant; with Nx = 1 every source lies
+// in the same column and the pull is cell + e_x.
+template <class SET, typename S, typename C, int A, class PTR>
+__device__ __forceinline__ C pull_col(const KParams<C>& k, const PTR& sp, int cell, int x,
+                                      int Nx) {
+    constexpr int EX = plane_ex<SET>(A);
+    int i;
+    if constexpr (EX == 0) {
+        i = cell;
+    } else if constexpr (EX > 0) {
+        i = cell + (x < EX ? Nx : 0);
+    } else {
+        i = cell + (x < Nx + EX ? 0 : -Nx);
+    }
+    return ld_pop<S, C>(k, static_cast<const S*>(sp[A])[i], A);
+}
+
+template <class SET, typename S, typename C, int A, class PTR>
+__device__ __forceinline__ C pull_col1(const KParams<C>& k, const PTR& sp, int cell) {
+    return ld_pop<S, C>(k, static_cast<const S*>(sp[A])[cell + plane_ex<SET>(A)], A);
+}
+
+template <class SET, typename S, typename C, class PTR, int... I>
+__device__ __forceinline__ void pull_rows_ct(const KParams<C>& k, const PTR& sp, int cell,
+                                             C* f, std::integer_sequence<int, I...>) {
+    const int Nx = k.Nx;
+    if (Nx == 1) {
+        ((f[I] = pull_col1<SET, S, C, I, PTR>(k, sp, cell)), ...);
+    } else {
+        const int x = cell % Nx;
+        ((f[I] = pull_col<SET, S, C, I, PTR>(k, sp, cell, x, Nx)), ...);
+    }
+}
+
+// Rows-path pull of a compiled set: the compile-time forms where they apply.
+template <class SET, typename S, typename C, class PTR>
+__device__ __forceinline__ void pull_rows_any(const KParams<C>& k, const PTR& sp, int cell, C* f) {
+    constexpr int V = SET::R + 2 * SET::P;
+    if (k.Nx == 1 || k.Nx >= k.maxex)
+        pull_rows_ct<SET, S, C>(k, sp, cell, f, std::make_integer_sequence<int, V>{});
+    else
+        pull_rows<V, S, C>(k, sp, cell, f);
+}
+
 // Fused step for a compiled velocity set: the V populations stay in registers
 // between the moment pass and the relaxation pass.
 //  - fast path (block-uniform): the block's nodes lie in one row at least
@@ -363,12 +416,15 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
         for (int a = 0; a < V; ++a) f[a] = ld_pop<S, C>(k, static_cast<const S*>(k.srcf[a])[cell], a);
     } else if (rows) {
         if (cell >= k.ncell) return;
-        pull_rows<V, S, C>(k, k.srcf, cell, f);
+        pull_rows_any<SET, S, C>(k, k.srcf, cell, f);
     } else {
         if (cell >= k.ncell) return;
         const int y = cell / k.Nx;
         const int x = cell - y * k.Nx;
         const bool nb = y < k.maxey, nt = y >= k.Ny - k.maxey;
+        if (!nb && !nt) {          // a node away from the walls in a tile that touches one
+            pull_rows_any<SET, S, C>(k, k.srcf, cell, f);
+        } else {
         const double pb = nb ? wall_dpsi<S, C>(k, src, x, true) : 0.0;
         const double pt = nt ? wall_dpsi<S, C>(k, src, x, false) : 0.0;
 #pragma unroll
@@ -380,6 +436,7 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
                 f[a] = C(pt * k.w[a]);
             else
                 f[a] = pull<S, C>(k, src, a, x, y);
+        }
         }
     }
     C drho = R ? f[0] : C(0), Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;

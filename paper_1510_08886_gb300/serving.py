@@ -140,11 +140,12 @@ class ContinuousBatcher:
         now = self.clock()
         finished = []
         for slot, r in self.active.items():
-            steps, _ = self.engine.info(slot)
+            r.steps += self.engine.chunk          # every resident solve ran the chunk
+            steps = r.steps
             du = float(res[slot, 0])
             status = 0 if math.isfinite(du) else -5      # a non-finite state makes du NaN
             if status != 0 or du < r.tol or steps >= self.max_steps:
-                r.steps, r.status, r.du = steps, status, du
+                r.status, r.du = status, du
                 r.converged = status == 0 and du < r.tol
                 r.mdot, r.us = float(res[slot, 1]), float(res[slot, 2])
                 r.t_done = now
