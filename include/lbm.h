@@ -241,6 +241,16 @@ int lbm_engine_remove(lbm_engine* e, int slot);
 /* Steps per chunk, even, 2..1000 (default 100). */
 int lbm_engine_set_chunk(lbm_engine* e, int steps);
 
+/* Resident chunks on (1, the default) or off (0).  When on, solves whose
+ * populations fit in one block's shared memory (V Nx (Ny + 2 max|e_y|)
+ * elements, at most 4096 nodes) are packed into bundles, and each bundle
+ * advances a whole chunk inside shared memory (one launch per chunk and
+ * velocity set), reading and writing device memory once per chunk.  The
+ * other solves take one tiled launch per step.  Both give bitwise the same
+ * results.  Takes effect at the next lbm_engine_run or
+ * lbm_engine_autotune.  LBM_EINVAL unless enable is 0 or 1. */
+int lbm_engine_set_resident(lbm_engine* e, int enable);
+
 /* Advance every resident solve by chunks * K steps, then copy the per-slot
  * results to `results` (host, 4 * max_solves doubles, may be NULL):
  * results[4 s + 0] = max |u_x(t) - u_x(t - dt)| over the last step,
@@ -262,6 +272,18 @@ int lbm_engine_moments(lbm_engine* e, int slot, double* rho, double* ux, double*
 
 /* Largest contiguous free block of the arena. */
 int lbm_engine_free_bytes(lbm_engine* e, size_t* largest);
+
+/* Checkpoint of one slot: a 64-byte header (V, Nx, Ny, precision, steps),
+ * the populations in storage format (V planes of Nx Ny elements, deviation
+ * form as lbm_populations describes) and the four fp64 moment fields (rho,
+ * u_x, u_y, previous u_x).  lbm_engine_state_bytes gives the size.
+ * lbm_engine_set_state restores into a slot holding a solve of the same
+ * velocity set, order, size and precision (LBM_EINVAL otherwise); fp32 solves
+ * then continue bit-identically, 16-bit solves continue with the stochastic
+ * rounding stream of their new slot.  Both synchronise the engine's stream. */
+int lbm_engine_state_bytes(lbm_engine* e, int slot, size_t* bytes);
+int lbm_engine_get_state(lbm_engine* e, int slot, void* host, size_t bytes);
+int lbm_engine_set_state(lbm_engine* e, int slot, const void* host, size_t bytes);
 
 /* ---- observables without allocation ------------------------------------ */
 

@@ -269,10 +269,12 @@ class Engine:
     or the slot table is full), advanced with ``run`` in chunks of
     ``chunk`` steps (one CUDA-graph replay per chunk) and released with
     ``remove``.  The arena is a torch uint8 tensor on the current device.
+    ``resident`` runs solves that fit in shared memory a whole chunk per
+    launch (bitwise the same results as the per-step launches).
     """
 
     def __init__(self, precision="fp32", max_solves=256, arena_bytes=1 << 30, stream=None,
-                 chunk=100):
+                 chunk=100, resident=True):
         torch = _torch_cuda()
         self._torch = torch
         self.precision = precision
@@ -289,6 +291,7 @@ class Engine:
         self._dvms = {}
         self.results = np.zeros((self.max_solves, 4))
         self.set_chunk(chunk)
+        self.set_resident(resident)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -312,6 +315,11 @@ class Engine:
     def set_chunk(self, steps):
         check(_lib.lib().lbm_engine_set_chunk(self._h, int(steps)), "lbm_engine_set_chunk")
         self.chunk = int(steps)
+
+    def set_resident(self, enable):
+        check(_lib.lib().lbm_engine_set_resident(self._h, int(bool(enable))),
+              "lbm_engine_set_resident")
+        self.resident = bool(enable)
 
     def add(self, e, w, c, order, Nx, Ny, Kn, force, rho=None):
         d = _DVM(e, w, c)
@@ -359,6 +367,22 @@ class Engine:
         check(_lib.lib().lbm_engine_moments(self._h, int(slot), _dp(rho), _dp(ux), _dp(uy)),
               "lbm_engine_moments")
         return rho, ux, uy
+
+    def get_state(self, slot):
+        """Checkpoint of a slot (header, populations, moment fields) as a uint8 array."""
+        n = ctypes.c_size_t(0)
+        check(_lib.lib().lbm_engine_state_bytes(self._h, int(slot), ctypes.byref(n)),
+              "lbm_engine_state_bytes")
+        buf = np.empty(n.value, dtype=np.uint8)
+        check(_lib.lib().lbm_engine_get_state(self._h, int(slot), buf.ctypes.data_as(ctypes.c_void_p),
+                                              buf.nbytes), "lbm_engine_get_state")
+        return buf
+
+    def set_state(self, slot, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(_lib.lib().lbm_engine_set_state(self._h, int(slot), buf.ctypes.data_as(ctypes.c_void_p),
+                                              buf.nbytes), "lbm_engine_set_state")
+        return self
 
     def free_bytes(self):
         n = ctypes.c_size_t(0)

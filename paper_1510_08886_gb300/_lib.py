@@ -67,6 +67,13 @@ SIGNATURES = {
                                       ctypes.c_double, c_double_p, c_int_p]),
     "lbm_engine_remove": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_engine_set_chunk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lbm_engine_set_resident": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lbm_engine_state_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_engine_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_size_t]),
+    "lbm_engine_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_size_t]),
     "lbm_engine_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p]),
     "lbm_engine_autotune": (ctypes.c_int, [ctypes.c_void_p, c_double_p]),
     "lbm_engine_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_long_p, c_int_p]),

@@ -38,13 +38,15 @@ template <class SET, int N, typename S, typename C>
 __global__ void __launch_bounds__(kBlock, min_blocks_for(SET::R + 2 * SET::P + (SET::P > 20 ? 24 : 12),
                                                          sizeof(C)))
 k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __restrict__ tiles,
-              const int* __restrict__ ntiles_p, int* __restrict__ counter,
+              const int* __restrict__ ntiles_p, const int* __restrict__ tile_off_p,
+              int* __restrict__ counter,
               const unsigned int* __restrict__ seed_p, int parity, int emit, int chunk) {
     constexpr int R = SET::R, P = SET::P, V = R + 2 * P;
     __shared__ const S* sp[V];
     __shared__ S* dp[V];
     __shared__ int s_first;
     const int ntiles = *ntiles_p;
+    tiles += *tile_off_p;
     const unsigned seed = *seed_p + unsigned(parity);
     int cur_slot = -1;
     for (;;) {
@@ -123,6 +125,290 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
                 B.prev[cell] = (double)q.ux;
             }
             flag_density<C>(q, B.status);
+        }
+    }
+}
+
+// ---- resident chunks ----------------------------------------------------------
+// Channels small enough for shared memory run a whole chunk of K steps there:
+// one block loads a bundle of such channels once, advances them K steps with
+// one barrier per step, and writes the state back once.  Streaming is in
+// place with the two-step (A/B) pattern on the +-e pairs: in a B step node n
+// reads population a from slot (n - e_a, abar) and writes its post-collision
+// value to (n + e_a, a); in an A step it reads (n, a) and writes (n, abar).
+// Each node's read set equals its write set, so no node overwrites a value
+// another node still has to read.  Populations that leave through a wall in a
+// B step land in maxey ghost rows beyond the wall, where the next A step's
+// flux balance (Eq. nm.15) finds them; in a B step the leaving populations
+// of the previous A step sit untouched in their source nodes.  Loads, fills,
+// moment sums, relaxation and roundings are those of k_engine_step, in the
+// same order, so the results are bitwise those of the tiled kernel.
+
+constexpr int kResMaxCh = 64;      // channels per bundle
+constexpr int kResNodes = 4096;    // padded nodes per bundle (channels start at multiples of 32)
+
+struct ResChannel {
+    int slot;
+    int start;      // first node in the bundle's node numbering (a multiple of 32)
+    int off;        // element offset of the channel's planes in shared memory
+    int ncell;
+};
+
+struct ResBundle {
+    int first;      // channels [first, first + count) of the channel list
+    int count;
+    int nodes;      // padded node count
+    int pad;
+};
+
+template <class SET>
+__host__ __device__ constexpr int plane_ey(int a) {
+    return a < SET::R ? 0 : (a < SET::R + SET::P ? SET::ey[a - SET::R] : -SET::ey[a - SET::R - SET::P]);
+}
+
+template <class SET>
+__host__ __device__ constexpr int plane_opp(int a) {
+    return a < SET::R ? a : (a < SET::R + SET::P ? a + SET::P : a - SET::P);
+}
+
+template <class SET>
+__host__ __device__ constexpr int set_maxey() {
+    int m = 0;
+    for (int p = 0; p < SET::P; ++p) m = SET::ey[p] > m ? SET::ey[p] : (-SET::ey[p] > m ? -SET::ey[p] : m);
+    return m;
+}
+
+template <class SET>
+__host__ __device__ constexpr int res_threads() {
+    return SET::R + 2 * SET::P <= 16 ? 1024 : 512;
+}
+
+// (x + d) mod Nx for x in [0, Nx); mode 0: Nx = 1, 1: Nx >= |d|, 2: any Nx
+template <int D, int MODE>
+__device__ __forceinline__ int xwrap(int x, int Nx) {
+    if constexpr (D == 0 || MODE == 0) {
+        return MODE == 0 ? 0 : x;
+    } else if constexpr (MODE == 1) {
+        const int t = x + D;
+        if constexpr (D > 0) return t >= Nx ? t - Nx : t;
+        else return t < 0 ? t + Nx : t;
+    } else {
+        const int t = (x + D) % Nx;
+        return t < 0 ? t + Nx : t;
+    }
+}
+
+// Flux balance of Eq. nm.15 for landing column x from shared memory: the
+// same sum, in the same order, as wall_dpsi.  In a B step the leaving
+// population b of node m = (x - e_x, j) sits at (m, bbar); in an A step it
+// sits in the ghost row at (m + e_b, b).
+template <typename S, typename C>
+__device__ __noinline__ double res_wall_dpsi(const KParams<C>& k, const S* sb, int PS, int G, int x,
+                                             bool bottom, bool stepA) {
+    const int Nx = k.Nx;
+    double acc = 0.0;
+    for (int b = k.R; b < k.V; ++b) {
+        const int ey = k.ey[b];
+        if (bottom ? (ey >= 0) : (ey <= 0)) continue;
+        const int n = bottom ? -ey : ey;
+        const int bb = b < k.R + k.P ? b + k.P : b - k.P;
+        int xs = x - k.sx[b];
+        xs += (xs < 0) ? Nx : 0;
+        for (int j = 0; j < n; ++j) {
+            const int row = bottom ? j : (k.Ny - 1 - j);
+            const S v = stepA ? sb[(long long)b * PS + (long long)(row + ey + G) * Nx + x]
+                              : sb[(long long)bb * PS + (long long)(row + G) * Nx + xs];
+            acc += (double)ld_pop<S, C>(k, v, b);
+        }
+    }
+    return acc * k.inv_den;
+}
+
+template <class SET, typename S, typename C, int MODE, bool STEP_A, int... I>
+__device__ __forceinline__ void res_pull(const KParams<C>& k, const S* sb, int PS, int x, int y,
+                                         C* f, std::integer_sequence<int, I...>) {
+    constexpr int G = set_maxey<SET>();
+    const int Nx = k.Nx;
+    if constexpr (STEP_A) {
+        const int o = (y + G) * Nx + x;
+        ((f[I] = ld_pop<S, C>(k, sb[I * PS + o], I)), ...);
+    } else {
+        ((f[I] = ld_pop<S, C>(k, sb[plane_opp<SET>(I) * PS + (y - plane_ey<SET>(I) + G) * Nx +
+                                    xwrap<-plane_ex<SET>(I), MODE>(x, Nx)], I)), ...);
+    }
+}
+
+template <class SET, typename S, typename C, int MODE, bool STEP_A, int... I>
+__device__ __forceinline__ void res_push(const KParams<C>& k, S* sb, int PS, int x, int y, const C* f,
+                                         unsigned rs, std::integer_sequence<int, I...>) {
+    constexpr int G = set_maxey<SET>();
+    const int Nx = k.Nx;
+    if constexpr (STEP_A) {
+        const int o = (y + G) * Nx + x;
+        ((sb[plane_opp<SET>(I) * PS + o] = st_pop<S, C>(k, f[I], I, rs)), ...);
+    } else {
+        ((sb[I * PS + (y + plane_ey<SET>(I) + G) * Nx + xwrap<plane_ex<SET>(I), MODE>(x, Nx)] =
+              st_pop<S, C>(k, f[I], I, rs)), ...);
+    }
+}
+
+// One node of one A or B step.
+template <class SET, int N, typename S, typename C, bool STEP_A>
+__device__ __forceinline__ void res_node(const EngineSolve<C>& B, S* sb, int slot, int cell,
+                                         unsigned seed, int emit) {
+    constexpr int R = SET::R, P = SET::P, V = R + 2 * P, G = set_maxey<SET>();
+    const KParams<C>& k = B.k;
+    const int Nx = k.Nx, Ny = k.Ny;
+    const int PS = Nx * (Ny + 2 * G);
+    const int y = cell / Nx;
+    const int x = cell - y * Nx;
+    C f[V];
+    const int mode = Nx == 1 ? 0 : (Nx >= k.maxex ? 1 : 2);
+    if (y >= G && y < Ny - G) {
+        if (mode == 0)
+            res_pull<SET, S, C, 0, STEP_A>(k, sb, PS, x, y, f, std::make_integer_sequence<int, V>{});
+        else if (mode == 1)
+            res_pull<SET, S, C, 1, STEP_A>(k, sb, PS, x, y, f, std::make_integer_sequence<int, V>{});
+        else
+            res_pull<SET, S, C, 2, STEP_A>(k, sb, PS, x, y, f, std::make_integer_sequence<int, V>{});
+    } else {
+        const bool nb = y < G, nt = y >= Ny - G;
+        const double pb = nb ? res_wall_dpsi<S, C>(k, sb, PS, G, x, true, STEP_A) : 0.0;
+        const double pt = nt ? res_wall_dpsi<S, C>(k, sb, PS, G, x, false, STEP_A) : 0.0;
+#pragma unroll
+        for (int a = 0; a < V; ++a) {
+            const int ys = y - k.ey[a];
+            if (ys < 0) {
+                f[a] = C(pb * k.w[a]);
+            } else if (ys >= Ny) {
+                f[a] = C(pt * k.w[a]);
+            } else if (STEP_A) {
+                f[a] = ld_pop<S, C>(k, sb[(long long)a * PS + (long long)(y + G) * Nx + x], a);
+            } else {
+                int xs = x - k.sx[a];
+                xs += (xs < 0) ? Nx : 0;
+                const int ab = a < R ? a : (a < R + P ? a + P : a - P);
+                f[a] = ld_pop<S, C>(k, sb[(long long)ab * PS + (long long)(ys + G) * Nx + xs], a);
+            }
+        }
+    }
+    C drho = R ? f[0] : C(0), Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
+    moments_ct<SET, C>(f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, P>{});
+    const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, Kxy, Kyy);
+    if (R) f[0] = fma(k.one_m_omega, f[0], k.omw_rest * q.a0);
+    if (k.force)
+        relax_ct<SET, N, true, C>(k, q, f, std::make_integer_sequence<int, P>{});
+    else
+        relax_ct<SET, N, false, C>(k, q, f, std::make_integer_sequence<int, P>{});
+    const unsigned rs = sr_seed<S, C>(seed + unsigned(slot) * 0x632be5abu, cell);
+    if (mode == 0)
+        res_push<SET, S, C, 0, STEP_A>(k, sb, PS, x, y, f, rs, std::make_integer_sequence<int, V>{});
+    else if (mode == 1)
+        res_push<SET, S, C, 1, STEP_A>(k, sb, PS, x, y, f, rs, std::make_integer_sequence<int, V>{});
+    else
+        res_push<SET, S, C, 2, STEP_A>(k, sb, PS, x, y, f, rs, std::make_integer_sequence<int, V>{});
+    if (emit == 1) {
+        B.rho[cell] = 1.0 + (double)q.drho;
+        B.ux[cell] = (double)q.ux;
+        B.uy[cell] = (double)q.uy;
+    } else if (emit == 2) {
+        B.prev[cell] = (double)q.ux;
+    }
+    flag_density<C>(q, B.status);
+}
+
+// Persistent blocks (one per SM) take bundles from an atomic counter; each
+// bundle runs K (even) steps: B, A, B, A, ...  Step i uses the seed and the
+// emit flags of step i of the tiled chunk.
+template <class SET, int N, typename S, typename C>
+__global__ void __launch_bounds__(res_threads<SET>(), 1)
+k_engine_resident(const EngineSolve<C>* __restrict__ solves, const ResBundle* __restrict__ bundles,
+                  const ResChannel* __restrict__ chans, const int* __restrict__ nbundles_p,
+                  const int* __restrict__ bundle_off_p, int* __restrict__ counter,
+                  const unsigned* __restrict__ seed_p, int K) {
+    constexpr int R = SET::R, P = SET::P, V = R + 2 * P, G = set_maxey<SET>();
+    constexpr int BT = res_threads<SET>();
+    constexpr int NPT = kResNodes / BT;
+    extern __shared__ __align__(16) unsigned char res_smem[];
+    S* const sm = reinterpret_cast<S*>(res_smem);
+    __shared__ ResChannel sch[kResMaxCh];
+    __shared__ int wch[kResNodes / 32];     // channel of each run of 32 nodes, -1: padding
+    __shared__ int s_b;
+    const int nb = *nbundles_p;
+    bundles += *bundle_off_p;
+    const unsigned seed0 = *seed_p;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_b = atomicAdd(counter, 1);
+        __syncthreads();
+        const int bi = s_b;
+        if (bi >= nb) break;
+        const ResBundle bd = bundles[bi];
+        for (int c = threadIdx.x; c < bd.count; c += BT) sch[c] = chans[bd.first + c];
+        for (int w = threadIdx.x; w < kResNodes / 32; w += BT) wch[w] = -1;
+        __syncthreads();
+        for (int c = threadIdx.x; c < bd.count; c += BT)
+            for (int w = sch[c].start >> 5; w < (sch[c].start + sch[c].ncell + 31) >> 5; ++w) wch[w] = c;
+        __syncthreads();
+        // load: the state (post-collision values at their own nodes) goes to
+        // the opposite planes, as an A step leaves it
+#pragma unroll 1
+        for (int j = 0; j < NPT; ++j) {
+            const int g = threadIdx.x + j * BT;
+            if (g >= bd.nodes) break;
+            const int c = wch[g >> 5];
+            if (c < 0) continue;
+            const ResChannel ch = sch[c];
+            const int cell = g - ch.start;
+            if (cell >= ch.ncell) continue;
+            const EngineSolve<C>& B = solves[ch.slot];
+            const int Nx = B.k.Nx, PS = Nx * (B.k.Ny + 2 * G);
+            const int y = cell / Nx, x = cell - y * Nx;
+            const S* src = static_cast<const S*>(B.f[B.phase]);
+            S* sb = sm + ch.off;
+#pragma unroll
+            for (int a = 0; a < V; ++a)
+                sb[plane_opp<SET>(a) * PS + (y + G) * Nx + x] = src[(long long)a * B.k.plane + cell];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int i = 0; i < K; ++i) {
+            const unsigned seed = seed0 + unsigned(i & 1);
+            const int emit = i == K - 1 ? 1 : (i == K - 2 ? 2 : 0);
+#pragma unroll 1
+            for (int j = 0; j < NPT; ++j) {
+                const int g = threadIdx.x + j * BT;
+                if (g >= bd.nodes) break;
+                const int c = wch[g >> 5];
+                if (c < 0) continue;
+                const ResChannel ch = sch[c];
+                const int cell = g - ch.start;
+                if (cell >= ch.ncell) continue;
+                if (i & 1)
+                    res_node<SET, N, S, C, true>(solves[ch.slot], sm + ch.off, ch.slot, cell, seed, emit);
+                else
+                    res_node<SET, N, S, C, false>(solves[ch.slot], sm + ch.off, ch.slot, cell, seed, emit);
+            }
+            __syncthreads();
+        }
+        // store: after the final A step population a of node n is at (n, abar)
+#pragma unroll 1
+        for (int j = 0; j < NPT; ++j) {
+            const int g = threadIdx.x + j * BT;
+            if (g >= bd.nodes) break;
+            const int c = wch[g >> 5];
+            if (c < 0) continue;
+            const ResChannel ch = sch[c];
+            const int cell = g - ch.start;
+            if (cell >= ch.ncell) continue;
+            const EngineSolve<C>& B = solves[ch.slot];
+            const int Nx = B.k.Nx, PS = Nx * (B.k.Ny + 2 * G);
+            const int y = cell / Nx, x = cell - y * Nx;
+            S* dst = static_cast<S*>(B.f[B.phase]);
+            const S* sb = sm + ch.off;
+#pragma unroll
+            for (int a = 0; a < V; ++a)
+                dst[(long long)a * B.k.plane + cell] = sb[plane_opp<SET>(a) * PS + (y + G) * Nx + x];
         }
     }
 }

@@ -8,8 +8,9 @@ namespace lbm {
 
 struct EngineLaunch {
     const void* solves;        // EngineSolve<float>*
-    const EngineTile* tiles;   // this group's tiles
+    const EngineTile* tiles;   // all tiles
     const int* ntiles;         // device count of this group's tiles
+    const int* tile_off;       // device offset of this group's tiles
     int* counter;              // work counter of this (step, group)
     const unsigned* seed;
     int parity, emit, chunk;
@@ -19,7 +20,7 @@ struct EngineLaunch {
 template <class SET, int N, typename S>
 cudaError_t engine_step_one(const EngineLaunch& L, cudaStream_t st) {
     k_engine_step<SET, N, S, float><<<L.grid, kBlock, 0, st>>>(
-        static_cast<const EngineSolve<float>*>(L.solves), L.tiles, L.ntiles, L.counter, L.seed,
+        static_cast<const EngineSolve<float>*>(L.solves), L.tiles, L.ntiles, L.tile_off, L.counter, L.seed,
         L.parity, L.emit, L.chunk);
     return cudaGetLastError();
 }
@@ -45,6 +46,90 @@ cudaError_t engine_step_t(int set_id, int N, const EngineLaunch& L, cudaStream_t
         case 5: return engine_step_n<SetD2V48, S>(N, L, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+struct ResidentLaunch {
+    const void* solves;        // EngineSolve<float>*
+    const ResBundle* bundles;  // all bundles (each group's largest first)
+    const ResChannel* chans;
+    const int* nbundles;       // device count of this group's bundles
+    const int* bundle_off;     // device offset of this group's bundles
+    int* counter;              // bundle counter of this chunk and group
+    const unsigned* seed;
+    int K;
+    int grid;
+    size_t smem;               // dynamic shared memory per block
+};
+
+template <class SET, int N, typename S>
+const void* resident_fn() {
+    return reinterpret_cast<const void*>(&k_engine_resident<SET, N, S, float>);
+}
+
+template <class SET, int N, typename S>
+cudaError_t resident_one(const ResidentLaunch& L, cudaStream_t st) {
+    k_engine_resident<SET, N, S, float><<<L.grid, res_threads<SET>(), L.smem, st>>>(
+        static_cast<const EngineSolve<float>*>(L.solves), L.bundles, L.chans, L.nbundles, L.bundle_off, L.counter,
+        L.seed, L.K);
+    return cudaGetLastError();
+}
+
+// Opt the resident kernel of (set, N) into `smem` bytes of dynamic shared
+// memory and return its resident blocks per SM at that size (0: unusable).
+template <class SET, int N, typename S>
+int resident_attr_one(size_t smem) {
+    const void* fn = resident_fn<SET, N, S>();
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_engine_resident<SET, N, S, float>,
+                                                      res_threads<SET>(), smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return b;
+}
+
+#define LBM_RES_DISPATCH(CALL)                                              \
+    switch (set_id * 3 + (N - 2)) {                                         \
+        case 0: return CALL(SetD2V16, 2);                                   \
+        case 1: return CALL(SetD2V16, 3);                                   \
+        case 2: return CALL(SetD2V16, 4);                                   \
+        case 3: return CALL(SetD2V32, 2);                                   \
+        case 4: return CALL(SetD2V32, 3);                                   \
+        case 5: return CALL(SetD2V32, 4);                                   \
+        case 6: return CALL(SetD2V33, 2);                                   \
+        case 7: return CALL(SetD2V33, 3);                                   \
+        case 8: return CALL(SetD2V33, 4);                                   \
+        case 9: return CALL(SetD2V53, 2);                                   \
+        case 10: return CALL(SetD2V53, 3);                                  \
+        case 11: return CALL(SetD2V53, 4);                                  \
+        case 12: return CALL(SetD2V40, 2);                                  \
+        case 13: return CALL(SetD2V40, 3);                                  \
+        case 14: return CALL(SetD2V40, 4);                                  \
+        case 15: return CALL(SetD2V48, 2);                                  \
+        case 16: return CALL(SetD2V48, 3);                                  \
+        case 17: return CALL(SetD2V48, 4);                                  \
+        default: break;                                                     \
+    }
+
+template <typename S>
+cudaError_t engine_resident_t(int set_id, int N, const ResidentLaunch& L, cudaStream_t st) {
+#define LBM_RES_LAUNCH(SET, NN) resident_one<SET, NN, S>(L, st)
+    LBM_RES_DISPATCH(LBM_RES_LAUNCH)
+#undef LBM_RES_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+template <typename S>
+int engine_resident_attr_t(int set_id, int N, size_t smem) {
+#define LBM_RES_ATTR(SET, NN) resident_attr_one<SET, NN, S>(smem)
+    LBM_RES_DISPATCH(LBM_RES_ATTR)
+#undef LBM_RES_ATTR
+    return 0;
 }
 
 // resident blocks per SM of the engine kernel of (set, N)

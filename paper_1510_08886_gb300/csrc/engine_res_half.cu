@@ -1,0 +1,14 @@
+// Resident-chunk engine kernels, IEEE half population storage.
+#include "engine_launch.cuh"
+
+namespace lbm {
+
+cudaError_t engine_resident_half(int set_id, int N, const ResidentLaunch& L, cudaStream_t st) {
+    return engine_resident_t<__half>(set_id, N, L, st);
+}
+
+int engine_resident_attr_half(int set_id, int N, size_t smem) {
+    return engine_resident_attr_t<__half>(set_id, N, smem);
+}
+
+}  // namespace lbm

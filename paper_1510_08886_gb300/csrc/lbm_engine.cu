@@ -1,8 +1,10 @@
 // Host side of the multi-solve engine (include/lbm.h, "engine" section):
 // a device arena with first-fit allocation (admission by footprint), slots
-// that can be added and removed between chunks, per-velocity-set tile lists,
-// CUDA-graph capture of a chunk of time steps plus the per-solve reductions,
-// and an autotuner of the persistent grid size and the tiles taken per grab.
+// that can be added and removed between chunks, per-velocity-set work lists
+// (bundles of channels small enough to run a whole chunk in shared memory,
+// tiles of the others), CUDA-graph capture of a chunk of time steps plus the
+// per-solve reductions, and an autotuner of the persistent grid size and the
+// tiles taken per grab.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -16,9 +18,17 @@
 
 namespace lbm {
 cudaError_t engine_step_fp32(int set_id, int N, const EngineLaunch& L, cudaStream_t st);
-cudaError_t engine_step_fp16(int set_id, int N, bool bf16, const EngineLaunch& L, cudaStream_t st);
+cudaError_t engine_step_half(int set_id, int N, const EngineLaunch& L, cudaStream_t st);
+cudaError_t engine_step_bf16(int set_id, int N, const EngineLaunch& L, cudaStream_t st);
 int engine_occupancy_fp32(int set_id, int N);
-int engine_occupancy_fp16(int set_id, int N, bool bf16);
+int engine_occupancy_half(int set_id, int N);
+int engine_occupancy_bf16(int set_id, int N);
+cudaError_t engine_resident_fp32(int set_id, int N, const ResidentLaunch& L, cudaStream_t st);
+cudaError_t engine_resident_half(int set_id, int N, const ResidentLaunch& L, cudaStream_t st);
+cudaError_t engine_resident_bf16(int set_id, int N, const ResidentLaunch& L, cudaStream_t st);
+int engine_resident_attr_fp32(int set_id, int N, size_t smem);
+int engine_resident_attr_half(int set_id, int N, size_t smem);
+int engine_resident_attr_bf16(int set_id, int N, size_t smem);
 cudaError_t engine_reduce(const void* solves, const int* active, double* out, int nslots,
                           cudaStream_t st);
 cudaError_t engine_advance(unsigned int* seed, unsigned int by, cudaStream_t st);
@@ -94,6 +104,13 @@ SlotLayout slot_layout(int V, size_t ncell, size_t elem) {
     return L;
 }
 
+struct GroupWork {
+    int g;
+    bool tiled, res;       // the group has tiles / bundles
+    int grid, rgrid;       // persistent grids (set at capture)
+    bool operator==(const GroupWork& o) const { return g == o.g && tiled == o.tiled && res == o.res; }
+};
+
 struct EngSlot {
     bool used = false;
     lbm::SolveSpec spec;
@@ -139,8 +156,17 @@ struct lbm_engine {
     int grab = 4;              // tiles taken per atomic grab
     int sms = 0;
     bool tiles_dirty = true, graph_dirty = true;
-    std::vector<int> groups, group_off;        // present groups and their tile offsets
-    std::vector<int> grids;                    // persistent grid size per present group
+    // resident chunks
+    bool resident = true;
+    size_t res_smem = 0;                       // dynamic shared memory per resident block
+    int res_occ[kGroups];                      // resident blocks per SM, -1: not yet queried
+    lbm::ResBundle* d_bundles = nullptr;       // max_slots entries
+    lbm::ResChannel* d_chans = nullptr;        // max_slots entries
+    int* d_nbundles = nullptr;                 // per group: counts, then offsets
+    int* d_rcounters = nullptr;                // per group
+    cudaStream_t side = nullptr;               // fork of the chunk graph
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::vector<GroupWork> plan;               // present groups and their work
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -152,68 +178,199 @@ bool is16(int p) { return p == LBM_FP16 || p == LBM_BF16; }
 
 int occupancy(const lbm_engine* e, int group) {
     const int set = group / 3, N = group % 3 + 2;
-    const int b = is16(e->precision) ? lbm::engine_occupancy_fp16(set, N, e->precision == LBM_BF16)
-                                     : lbm::engine_occupancy_fp32(set, N);
+    const int b = e->precision == LBM_FP16   ? lbm::engine_occupancy_half(set, N)
+                  : e->precision == LBM_BF16 ? lbm::engine_occupancy_bf16(set, N)
+                                             : lbm::engine_occupancy_fp32(set, N);
     return std::max(1, b);
 }
 
+// resident blocks per SM of the group's resident kernel at res_smem (0: unusable)
+int res_occupancy(lbm_engine* e, int group) {
+    if (e->res_occ[group] < 0) {
+        const int set = group / 3, N = group % 3 + 2;
+        e->res_occ[group] =
+            e->precision == LBM_FP16   ? lbm::engine_resident_attr_half(set, N, e->res_smem)
+            : e->precision == LBM_BF16 ? lbm::engine_resident_attr_bf16(set, N, e->res_smem)
+                                       : lbm::engine_resident_attr_fp32(set, N, e->res_smem);
+    }
+    return e->res_occ[group];
+}
+
+// shared-memory footprint of a channel in a bundle: V planes of Nx (Ny + 2 maxey)
+size_t res_bytes(const lbm::SolveSpec& s) {
+    return size_t(s.V) * s.Nx * (s.Ny + 2 * s.maxey) * s.elem;
+}
+
+bool res_eligible(lbm_engine* e, const EngSlot& sl) {
+    const size_t n = size_t(sl.spec.Nx) * sl.spec.Ny;
+    return e->resident && res_bytes(sl.spec) <= e->res_smem &&
+           ((n + 31) & ~size_t(31)) <= size_t(lbm::kResNodes) && res_occupancy(e, sl.group) > 0;
+}
+
+// Work lists: per group, bundles of resident channels (first-fit decreasing by
+// shared-memory footprint, largest bundles first) and tiles of the others.
 int rebuild_tiles(lbm_engine* e) {
     std::vector<lbm::EngineTile> t;
-    std::vector<int> groups, offs;
-    std::vector<int> counts(kGroups, 0);
+    std::vector<lbm::ResBundle> bundles;
+    std::vector<lbm::ResChannel> chans;
+    std::vector<GroupWork> plan;
+    std::vector<int> counts(2 * kGroups, 0), nbund(2 * kGroups, 0);   // count, offset
+    struct Bin {
+        size_t bytes;
+        int nodes;
+        std::vector<int> members;
+    };
     for (int g = 0; g < kGroups; ++g) {
-        const size_t start = t.size();
+        const size_t start = t.size(), bstart = bundles.size();
+        std::vector<int> res;
         for (int s = 0; s < e->max_slots; ++s) {
             const EngSlot& sl = e->slots[s];
             if (!sl.used || sl.group != g) continue;
+            if (res_eligible(e, sl)) {
+                res.push_back(s);
+                continue;
+            }
             const int n = sl.spec.Nx * sl.spec.Ny;
             for (int c0 = 0; c0 < n; c0 += lbm::kBlock) t.push_back({s, c0});
         }
-        if (t.size() > start) {
-            groups.push_back(g);
-            offs.push_back(int(start));
-            counts[g] = int(t.size() - start);
+        std::stable_sort(res.begin(), res.end(), [&](int a, int b) {
+            return res_bytes(e->slots[a].spec) > res_bytes(e->slots[b].spec);
+        });
+        std::vector<Bin> bins;
+        for (int s : res) {
+            const size_t by = res_bytes(e->slots[s].spec);
+            const int nd = (e->slots[s].spec.Nx * e->slots[s].spec.Ny + 31) & ~31;
+            Bin* dst = nullptr;
+            for (Bin& b : bins)
+                if (b.bytes + by <= e->res_smem && b.nodes + nd <= lbm::kResNodes &&
+                    int(b.members.size()) < lbm::kResMaxCh) {
+                    dst = &b;
+                    break;
+                }
+            if (!dst) {
+                bins.push_back(Bin{0, 0, {}});
+                dst = &bins.back();
+            }
+            dst->bytes += by;
+            dst->nodes += nd;
+            dst->members.push_back(s);
         }
+        std::stable_sort(bins.begin(), bins.end(),
+                         [](const Bin& a, const Bin& b) { return a.bytes > b.bytes; });
+        for (const Bin& b : bins) {
+            lbm::ResBundle rb{int(chans.size()), int(b.members.size()), 0, 0};
+            int off = 0;
+            for (int s : b.members) {
+                const lbm::SolveSpec& sp = e->slots[s].spec;
+                const int n = sp.Nx * sp.Ny;
+                chans.push_back({s, rb.nodes, off, n});
+                rb.nodes += (n + 31) & ~31;
+                off += int(res_bytes(sp) / sp.elem);
+            }
+            bundles.push_back(rb);
+        }
+        counts[g] = int(t.size() - start);
+        counts[kGroups + g] = int(start);
+        nbund[g] = int(bundles.size() - bstart);
+        nbund[kGroups + g] = int(bstart);
+        if (counts[g] || nbund[g]) plan.push_back({g, counts[g] > 0, nbund[g] > 0, 0, 0});
     }
-    if (t.size() > e->tile_cap) return LBM_ENOMEM;
+    if (t.size() > e->tile_cap || bundles.size() > size_t(e->max_slots)) return LBM_ENOMEM;
     cudaError_t err = cudaSuccess;
     if (!t.empty())
         err = cudaMemcpyAsync(e->d_tiles, t.data(), t.size() * sizeof(lbm::EngineTile),
                               cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess && !bundles.empty())
+        err = cudaMemcpyAsync(e->d_bundles, bundles.data(), bundles.size() * sizeof(lbm::ResBundle),
+                              cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess && !chans.empty())
+        err = cudaMemcpyAsync(e->d_chans, chans.data(), chans.size() * sizeof(lbm::ResChannel),
+                              cudaMemcpyHostToDevice, e->stream);
     if (err == cudaSuccess)
-        err = cudaMemcpyAsync(e->d_ntiles, counts.data(), kGroups * sizeof(int),
+        err = cudaMemcpyAsync(e->d_ntiles, counts.data(), 2 * kGroups * sizeof(int),
+                              cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(e->d_nbundles, nbund.data(), 2 * kGroups * sizeof(int),
                               cudaMemcpyHostToDevice, e->stream);
     if (err != cudaSuccess) return cuda_rc(err);
-    if (groups != e->groups) e->graph_dirty = true;
-    e->groups = groups;
-    e->group_off = offs;
+    // the graph reads counts and offsets from device memory: only a change of
+    // the launches themselves needs a new capture
+    if (!(plan == e->plan)) {
+        e->graph_dirty = true;
+        e->plan = plan;
+    }
     e->tiles_dirty = false;
     return LBM_OK;
 }
 
 // One chunk of K steps + the reductions + the seed advance, on the stream.
+// Resident bundles (K steps per launch) run on a fork of the stream beside
+// the per-step tiled launches; both touch disjoint solves.
 int enqueue_chunk(lbm_engine* e) {
-    cudaError_t err = cudaMemsetAsync(e->d_counters, 0, sizeof(int) * kGroups * e->K, e->stream);
+    bool any_t = false, any_r = false;
+    for (const GroupWork& w : e->plan) {
+        any_t |= w.tiled;
+        any_r |= w.res;
+    }
+    cudaError_t err = cudaSuccess;
+    if (any_t) err = cudaMemsetAsync(e->d_counters, 0, sizeof(int) * kGroups * e->K, e->stream);
+    if (any_r && err == cudaSuccess)
+        err = cudaMemsetAsync(e->d_rcounters, 0, sizeof(int) * kGroups, e->stream);
     if (err != cudaSuccess) return cuda_rc(err);
-    for (int i = 0; i < e->K; ++i) {
-        for (size_t gi = 0; gi < e->groups.size(); ++gi) {
-            const int g = e->groups[gi];
+    const bool fork = any_t && any_r;
+    cudaStream_t rs = fork ? e->side : e->stream;
+    if (fork) {
+        err = cudaEventRecord(e->ev_fork, e->stream);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(e->side, e->ev_fork, 0);
+        if (err != cudaSuccess) return cuda_rc(err);
+    }
+    for (const GroupWork& w : e->plan) {
+        if (!w.res) continue;
+        lbm::ResidentLaunch L{};
+        L.solves = e->d_solves;
+        L.bundles = e->d_bundles;
+        L.chans = e->d_chans;
+        L.nbundles = e->d_nbundles + w.g;
+        L.bundle_off = e->d_nbundles + kGroups + w.g;
+        L.counter = e->d_rcounters + w.g;
+        L.seed = e->d_seed;
+        L.K = e->K;
+        L.grid = w.rgrid;
+        L.smem = e->res_smem;
+        const int set = w.g / 3, N = w.g % 3 + 2;
+        err = e->precision == LBM_FP16   ? lbm::engine_resident_half(set, N, L, rs)
+              : e->precision == LBM_BF16 ? lbm::engine_resident_bf16(set, N, L, rs)
+                                         : lbm::engine_resident_fp32(set, N, L, rs);
+        if (err != cudaSuccess) return cuda_rc(err);
+    }
+    if (fork) {
+        err = cudaEventRecord(e->ev_join, e->side);
+        if (err != cudaSuccess) return cuda_rc(err);
+    }
+    for (int i = 0; i < e->K && any_t; ++i) {
+        for (const GroupWork& w : e->plan) {
+            if (!w.tiled) continue;
             lbm::EngineLaunch L{};
             L.solves = e->d_solves;
-            L.tiles = e->d_tiles + e->group_off[gi];
-            L.ntiles = e->d_ntiles + g;
-            L.counter = e->d_counters + i * kGroups + g;
+            L.tiles = e->d_tiles;
+            L.ntiles = e->d_ntiles + w.g;
+            L.tile_off = e->d_ntiles + kGroups + w.g;
+            L.counter = e->d_counters + i * kGroups + w.g;
             L.seed = e->d_seed;
             L.parity = i & 1;
             L.emit = i == e->K - 1 ? 1 : (i == e->K - 2 ? 2 : 0);
             L.chunk = e->grab;
-            L.grid = e->grids[gi];
-            const int set = g / 3, N = g % 3 + 2;
-            err = is16(e->precision)
-                      ? lbm::engine_step_fp16(set, N, e->precision == LBM_BF16, L, e->stream)
-                      : lbm::engine_step_fp32(set, N, L, e->stream);
+            L.grid = w.grid;
+            const int set = w.g / 3, N = w.g % 3 + 2;
+            err = e->precision == LBM_FP16   ? lbm::engine_step_half(set, N, L, e->stream)
+                  : e->precision == LBM_BF16 ? lbm::engine_step_bf16(set, N, L, e->stream)
+                                             : lbm::engine_step_fp32(set, N, L, e->stream);
             if (err != cudaSuccess) return cuda_rc(err);
         }
+    }
+    if (fork) {
+        err = cudaStreamWaitEvent(e->stream, e->ev_join, 0);
+        if (err != cudaSuccess) return cuda_rc(err);
     }
     err = lbm::engine_reduce(e->d_solves, e->d_active, e->d_results, e->max_slots, e->stream);
     if (err == cudaSuccess) err = lbm::engine_advance(e->d_seed, unsigned(e->K), e->stream);
@@ -221,9 +378,10 @@ int enqueue_chunk(lbm_engine* e) {
 }
 
 int recapture(lbm_engine* e) {
-    e->grids.clear();
-    for (int g : e->groups)
-        e->grids.push_back(std::max(1, int(std::lround(occupancy(e, g) * e->bps_factor))) * e->sms);
+    for (GroupWork& w : e->plan) {
+        w.grid = std::max(1, int(std::lround(occupancy(e, w.g) * e->bps_factor))) * e->sms;
+        w.rgrid = w.res ? std::max(1, res_occupancy(e, w.g)) * e->sms : 0;
+    }
     if (e->exec) {
         cudaGraphExecDestroy(e->exec);
         e->exec = nullptr;
@@ -250,7 +408,7 @@ int prepare(lbm_engine* e) {
         const int rc = rebuild_tiles(e);
         if (rc) return rc;
     }
-    if (e->graph_dirty && !e->groups.empty()) return recapture(e);
+    if (e->graph_dirty && !e->plan.empty()) return recapture(e);
     return LBM_OK;
 }
 
@@ -297,7 +455,11 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
     const size_t o_active = take(sizeof(int) * max_solves);
     const size_t o_results = take(sizeof(double) * 4 * max_solves);
     const size_t o_status = take(sizeof(unsigned) * max_solves);
-    const size_t o_ntiles = take(sizeof(int) * kGroups);
+    const size_t o_ntiles = take(sizeof(int) * 2 * kGroups);
+    const size_t o_nbundles = take(sizeof(int) * 2 * kGroups);
+    const size_t o_rcounters = take(sizeof(int) * kGroups);
+    const size_t o_bundles = take(sizeof(lbm::ResBundle) * max_solves);
+    const size_t o_chans = take(sizeof(lbm::ResChannel) * max_solves);
     const size_t o_counters = take(sizeof(int) * kGroups * kMaxChunk);
     const size_t o_seed = take(sizeof(unsigned));
     const size_t o_tiles = take(sizeof(lbm::EngineTile) * e->tile_cap);
@@ -316,6 +478,11 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
     e->d_results = reinterpret_cast<double*>(e->base + o_results);
     e->d_status = reinterpret_cast<unsigned*>(e->base + o_status);
     e->d_ntiles = reinterpret_cast<int*>(e->base + o_ntiles);
+    e->d_nbundles = reinterpret_cast<int*>(e->base + o_nbundles);
+    e->d_rcounters = reinterpret_cast<int*>(e->base + o_rcounters);
+    e->d_bundles = reinterpret_cast<lbm::ResBundle*>(e->base + o_bundles);
+    e->d_chans = reinterpret_cast<lbm::ResChannel*>(e->base + o_chans);
+    for (int g = 0; g < kGroups; ++g) e->res_occ[g] = -1;
     e->d_counters = reinterpret_cast<int*>(e->base + o_counters);
     e->d_seed = reinterpret_cast<unsigned*>(e->base + o_seed);
     e->d_tiles = reinterpret_cast<lbm::EngineTile*>(e->base + o_tiles);
@@ -326,6 +493,14 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, dev);
+    int optin = 0;
+    if (err == cudaSuccess)
+        err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // the resident kernels' static shared memory is under 2 KiB
+    e->res_smem = optin > 4096 ? size_t(optin - 4096) & ~size_t(255) : 0;
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->side, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming);
     if (err == cudaSuccess) {
         if (stream) {
             e->stream = static_cast<cudaStream_t>(stream);
@@ -348,6 +523,9 @@ void lbm_engine_destroy(lbm_engine* e) {
     if (!e) return;
     if (e->stream) cudaStreamSynchronize(e->stream);
     if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+    if (e->ev_join) cudaEventDestroy(e->ev_join);
+    if (e->side) cudaStreamDestroy(e->side);
     if (e->own_arena && e->base) cudaFree(e->base);
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
     delete e;
@@ -449,6 +627,15 @@ int lbm_engine_remove(lbm_engine* e, int slot) {
     return LBM_OK;
 }
 
+int lbm_engine_set_resident(lbm_engine* e, int enable) {
+    if (!e || (enable != 0 && enable != 1)) return LBM_EINVAL;
+    if (e->resident != (enable == 1)) {
+        e->resident = enable == 1;
+        e->tiles_dirty = true;
+    }
+    return LBM_OK;
+}
+
 int lbm_engine_set_chunk(lbm_engine* e, int steps) {
     if (!e || steps < 2 || steps > kMaxChunk || (steps & 1)) return LBM_EINVAL;
     if (steps != e->K) {
@@ -462,7 +649,7 @@ int lbm_engine_run(lbm_engine* e, int chunks, double* results) {
     if (!e || chunks < 0) return LBM_EINVAL;
     int rc = prepare(e);
     if (rc) return rc;
-    if (!e->groups.empty()) {
+    if (!e->plan.empty()) {
         for (int c = 0; c < chunks; ++c) {
             const cudaError_t err = cudaGraphLaunch(e->exec, e->stream);
             if (err != cudaSuccess) return cuda_rc(err);
@@ -477,7 +664,7 @@ int lbm_engine_autotune(lbm_engine* e, double* best_ms_per_step) {
     if (!e) return LBM_EINVAL;
     int rc = prepare(e);
     if (rc) return rc;
-    if (e->groups.empty()) return LBM_OK;
+    if (e->plan.empty()) return LBM_OK;
     const double factors[] = {1.0, 0.5};
     const int grabs[] = {1, 2, 4, 8, 16};
     double best = HUGE_VAL, bf = e->bps_factor;
@@ -537,6 +724,83 @@ int lbm_engine_moments(lbm_engine* e, int slot, double* rho, double* ux, double*
     if (ux && err == cudaSuccess) err = cudaMemcpyAsync(ux, h.ux, n, cudaMemcpyDeviceToHost, e->stream);
     if (uy && err == cudaSuccess) err = cudaMemcpyAsync(uy, h.uy, n, cudaMemcpyDeviceToHost, e->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    return cuda_rc(err);
+}
+
+namespace {
+
+struct EngineStateHeader {
+    char magic[8];          // "LBMENG1\0"
+    int V, Nx, Ny, precision, N, set_id;
+    long steps;
+    double tau, g;
+};
+static_assert(sizeof(EngineStateHeader) <= 64, "header fits its 64 bytes");
+
+size_t engine_state_bytes(const EngSlot& sl) {
+    const size_t n = size_t(sl.spec.Nx) * sl.spec.Ny;
+    return 64 + size_t(sl.spec.V) * n * sl.spec.elem + 4 * n * 8;
+}
+
+}  // namespace
+
+int lbm_engine_state_bytes(lbm_engine* e, int slot, size_t* bytes) {
+    if (!e || !bytes || slot < 0 || slot >= e->max_slots || !e->slots[slot].used) return LBM_EINVAL;
+    *bytes = engine_state_bytes(e->slots[slot]);
+    return LBM_OK;
+}
+
+int lbm_engine_get_state(lbm_engine* e, int slot, void* host, size_t bytes) {
+    if (!e || !host || slot < 0 || slot >= e->max_slots || !e->slots[slot].used) return LBM_EINVAL;
+    const EngSlot& sl = e->slots[slot];
+    if (bytes < engine_state_bytes(sl)) return LBM_EINVAL;
+    const lbm::EngineSolve<float>& h = e->h_solves[slot];
+    const size_t n = size_t(sl.spec.Nx) * sl.spec.Ny, pb = size_t(sl.spec.V) * n * sl.spec.elem;
+    EngineStateHeader hd{};
+    std::memcpy(hd.magic, "LBMENG1", 8);
+    hd.V = sl.spec.V;
+    hd.Nx = sl.spec.Nx;
+    hd.Ny = sl.spec.Ny;
+    hd.precision = e->precision;
+    hd.N = sl.spec.N;
+    hd.set_id = sl.spec.set_id;
+    hd.steps = sl.steps;
+    hd.tau = h.tau;
+    hd.g = h.g;
+    char* out = static_cast<char*>(host);
+    std::memset(out, 0, 64);
+    std::memcpy(out, &hd, sizeof(hd));
+    char* p = out + 64;
+    cudaError_t err = cudaMemcpyAsync(p, h.f[h.phase], pb, cudaMemcpyDeviceToHost, e->stream);
+    p += pb;
+    const double* fields[4] = {h.rho, h.ux, h.uy, h.prev};
+    for (int i = 0; i < 4 && err == cudaSuccess; ++i, p += n * 8)
+        err = cudaMemcpyAsync(p, fields[i], n * 8, cudaMemcpyDeviceToHost, e->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    return cuda_rc(err);
+}
+
+int lbm_engine_set_state(lbm_engine* e, int slot, const void* host, size_t bytes) {
+    if (!e || !host || slot < 0 || slot >= e->max_slots || !e->slots[slot].used) return LBM_EINVAL;
+    EngSlot& sl = e->slots[slot];
+    if (bytes < engine_state_bytes(sl)) return LBM_EINVAL;
+    EngineStateHeader hd{};
+    std::memcpy(&hd, host, sizeof(hd));
+    const lbm::EngineSolve<float>& h = e->h_solves[slot];
+    if (std::memcmp(hd.magic, "LBMENG1", 8) != 0 || hd.V != sl.spec.V || hd.Nx != sl.spec.Nx ||
+        hd.Ny != sl.spec.Ny || hd.precision != e->precision || hd.N != sl.spec.N ||
+        hd.set_id != sl.spec.set_id || hd.tau != h.tau || hd.g != h.g || hd.steps < 0)
+        return LBM_EINVAL;
+    const size_t n = size_t(sl.spec.Nx) * sl.spec.Ny, pb = size_t(sl.spec.V) * n * sl.spec.elem;
+    const char* p = static_cast<const char*>(host) + 64;
+    cudaError_t err = cudaMemcpyAsync(h.f[h.phase], p, pb, cudaMemcpyHostToDevice, e->stream);
+    p += pb;
+    double* fields[4] = {h.rho, h.ux, h.uy, h.prev};
+    for (int i = 0; i < 4 && err == cudaSuccess; ++i, p += n * 8)
+        err = cudaMemcpyAsync(fields[i], p, n * 8, cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(h.status, 0, sizeof(unsigned), e->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+    if (err == cudaSuccess) sl.steps = hd.steps;
     return cuda_rc(err);
 }
 

@@ -82,9 +82,16 @@ __device__ __forceinline__ unsigned sr_seed(unsigned seed, int cell) {
     else return 0u;
 }
 
+// Rounded product that the compiler never merges into an add (an FMA).
+// Every product in the collision arithmetic that meets an addition is either
+// an explicit fma or mul_rn, so each kernel that inlines these functions
+// rounds every node identically (no contraction choice is left open).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <typename S, typename C>
 __device__ __forceinline__ C ld_pop(const KParams<C>& k, S v, int a) {
-    if constexpr (Storage<S>::scaled) return Storage<S>::to_f(v) * k.sw[a];
+    if constexpr (Storage<S>::scaled) return mul_rn(Storage<S>::to_f(v), k.sw[a]);
     else return C(v);
 }
 
@@ -147,53 +154,58 @@ __device__ __forceinline__ CellCoef<C> cell_coef(const KParams<C>& k, C drho, C 
     q.rho = C(1) + drho;
     const C inv = C(1) / q.rho;
     // Eq. nm.10: rho u = sum fbar xi + (dt/2) rho g
-    q.ux = k.c * Jx * inv + k.hdt * k.gx;
-    q.uy = k.c * Jy * inv + k.hdt * k.gy;
-    q.utx = k.c * q.ux;
-    q.uty = k.c * q.uy;
-    const C u2 = q.ux * q.ux + q.uy * q.uy;
+    q.ux = fma(mul_rn(k.c, Jx), inv, mul_rn(k.hdt, k.gx));
+    q.uy = fma(mul_rn(k.c, Jy), inv, mul_rn(k.hdt, k.gy));
+    q.utx = mul_rn(k.c, q.ux);
+    q.uty = mul_rn(k.c, q.uy);
+    const C u2 = fma(q.ux, q.ux, mul_rn(q.uy, q.uy));
     // f0/(rho w) - 1 of Eq. nm.3 (+ the N = 4 Hermite term of Eq. equi.hermite)
     // with s = u.xi, t = s^2:
     //   even: (t - u2)/2 + [N>=4] (t^2 - 6 t u2 + 3 u2^2)/24
     //   odd:  s + [N>=3] s (t - 3 u2)/6
-    q.a0 = drho + q.rho * (C(-0.5) * u2 + (N >= 4 ? C(0.125) * u2 * u2 : C(0)));
-    q.a1 = q.rho * (C(0.5) - (N >= 4 ? C(0.25) * u2 : C(0)));
-    q.a2 = N >= 4 ? q.rho * C(1.0 / 24.0) : C(0);
-    q.b0 = q.rho * (N >= 3 ? C(1) - C(0.5) * u2 : C(1));
-    q.b1 = N >= 3 ? q.rho * C(1.0 / 6.0) : C(0);
-    q.tr = k.tau * q.rho;
+    // (products with powers of two are exact)
+    q.a0 = fma(q.rho, N >= 4 ? fma(C(0.125) * u2, u2, C(-0.5) * u2) : C(-0.5) * u2, drho);
+    q.a1 = mul_rn(q.rho, C(0.5) - (N >= 4 ? C(0.25) * u2 : C(0)));
+    q.a2 = N >= 4 ? mul_rn(q.rho, C(1.0 / 24.0)) : C(0);
+    q.b0 = N >= 3 ? mul_rn(q.rho, C(1) - C(0.5) * u2) : q.rho;
+    q.b1 = N >= 3 ? mul_rn(q.rho, C(1.0 / 6.0)) : C(0);
+    q.tr = mul_rn(k.tau, q.rho);
     if (k.force) {
         // even force part of Eq. nm.4: tau rho ((g.xi)(u.xi) - u.g)
-        q.a0 -= q.tr * (q.ux * k.gx + q.uy * k.gy);
+        q.a0 = fma(-q.tr, fma(q.ux, k.gx, mul_rn(q.uy, k.gy)), q.a0);
         // A = Pi - rho delta, Pi the momentum flux of f = (2 tau fbar + dt feq)
         // / (2 tau + dt) (Eq. nm.7 inverted), Pibar = delta + c^2 K and
         // Pi_eq = rho (delta + u u + tau (g u + u g)) (exact for Q >= N + 2):
         //   (2 tau + dt) A = -2 tau drho delta + 2 tau c^2 K
         //                    + dt rho (u u + tau (g u + u g))
-        const C tdr = k.dt * q.rho;
-        const C Axx = (k.two_tau * (k.c2 * Kxx - drho) +
-                       tdr * (q.ux * q.ux + C(2) * k.tau * k.gx * q.ux)) * k.inv_2tau_dt;
-        const C Ayy = (k.two_tau * (k.c2 * Kyy - drho) +
-                       tdr * (q.uy * q.uy + C(2) * k.tau * k.gy * q.uy)) * k.inv_2tau_dt;
-        const C Axy = (k.two_tau * k.c2 * Kxy +
-                       tdr * (q.ux * q.uy + k.tau * (k.gx * q.uy + k.gy * q.ux))) * k.inv_2tau_dt;
+        const C tdr = mul_rn(k.dt, q.rho);
+        const C tgx = mul_rn(k.two_tau, k.gx), tgy = mul_rn(k.two_tau, k.gy);
+        const C Axx = mul_rn(fma(k.two_tau, fma(k.c2, Kxx, -drho),
+                                 mul_rn(tdr, fma(q.ux, q.ux, mul_rn(tgx, q.ux)))), k.inv_2tau_dt);
+        const C Ayy = mul_rn(fma(k.two_tau, fma(k.c2, Kyy, -drho),
+                                 mul_rn(tdr, fma(q.uy, q.uy, mul_rn(tgy, q.uy)))), k.inv_2tau_dt);
+        const C Axy = mul_rn(fma(mul_rn(k.two_tau, k.c2), Kxy,
+                                 mul_rn(tdr, fma(q.ux, q.uy, mul_rn(k.tau, fma(k.gx, q.uy,
+                                                                              mul_rn(k.gy, q.ux)))))),
+                             k.inv_2tau_dt);
         if (N >= 3) {
             // third-order force term (1/2) A:((g.xi) H2(xi) - 2 g xi)
-            q.qxx = k.half_tau * k.c2 * Axx;
-            q.qxy = k.half_tau * k.c2 * Axy;   // multiplies 2 ex ey
-            q.qyy = k.half_tau * k.c2 * Ayy;
-            q.qtr = k.half_tau * (Axx + Ayy);
-            q.hx = k.tau * k.c * (k.gx * Axx + k.gy * Axy);
-            q.hy = k.tau * k.c * (k.gx * Axy + k.gy * Ayy);
+            const C htc2 = mul_rn(k.half_tau, k.c2), tc = mul_rn(k.tau, k.c);
+            q.qxx = mul_rn(htc2, Axx);
+            q.qxy = mul_rn(htc2, Axy);   // multiplies 2 ex ey
+            q.qyy = mul_rn(htc2, Ayy);
+            q.qtr = mul_rn(k.half_tau, Axx + Ayy);
+            q.hx = mul_rn(tc, fma(k.gx, Axx, mul_rn(k.gy, Axy)));
+            q.hy = mul_rn(tc, fma(k.gx, Axy, mul_rn(k.gy, Ayy)));
         } else {
             q.qxx = q.qxy = q.qyy = q.qtr = q.hx = q.hy = C(0);
         }
-        const C cg = k.c * k.gx;
-        q.trcg = q.tr * cg;
-        q.k0 = cg * (q.tr - q.qtr);
-        q.cqxx = cg * q.qxx;
-        q.cqxy = cg * q.qxy;
-        q.cqyy = cg * q.qyy;
+        const C cg = mul_rn(k.c, k.gx);
+        q.trcg = mul_rn(q.tr, cg);
+        q.k0 = mul_rn(cg, q.tr - q.qtr);
+        q.cqxx = mul_rn(cg, q.qxx);
+        q.cqxy = mul_rn(cg, q.qxy);
+        q.cqyy = mul_rn(cg, q.qyy);
     }
     return q;
 }
@@ -205,19 +217,19 @@ __device__ __forceinline__ void pair_update(const KParams<C>& k, const CellCoef<
                                             C& fp, C& fm) {
     const C ex = k.pex[p], ey = k.pey[p];
     const C s = fma(q.uty, ey, q.utx * ex);
-    const C t = s * s;
+    const C t = mul_rn(s, s);
     C Ge = fma(t, fma(t, q.a2, q.a1), q.a0);
-    C Go = s * fma(t, q.b1, q.b0);
+    C Go = mul_rn(s, fma(t, q.b1, q.b0));
     if (FORCE) {
         const C ge = k.pge[p];
         // odd force part: tau rho (g.xi) + (tau/2)((g.xi) Q - 2 (g.A).xi)
         const C halfQ = fma(q.qxx, k.pexx[p], fma(q.qxy, k.pexy2[p], fma(q.qyy, k.peyy[p], -q.qtr)));
-        Ge = fma(q.tr * ge, s, Ge);
+        Ge = fma(mul_rn(q.tr, ge), s, Ge);
         Go = fma(ge, q.tr + halfQ, Go) - fma(q.hx, ex, q.hy * ey);
     }
-    const C X = k.pomw[p] * Ge, Y = k.pomw[p] * Go;
-    fp = fma(k.one_m_omega, fp, X + Y);
-    fm = fma(k.one_m_omega, fm, X - Y);
+    const C X = mul_rn(k.pomw[p], Ge);
+    fp = fma(k.one_m_omega, fp, fma(k.pomw[p], Go, X));
+    fm = fma(k.one_m_omega, fm, fma(-k.pomw[p], Go, X));
 }
 
 template <typename C>
@@ -251,7 +263,7 @@ template <int E, typename C>
 __device__ __forceinline__ C mulc(C v) {          // E v, E != 0
     if constexpr (E == 1) return v;
     else if constexpr (E == -1) return -v;
-    else return C(E) * v;
+    else return mul_rn(C(E), v);
 }
 
 template <int E, typename C>
@@ -286,9 +298,9 @@ __device__ __forceinline__ void moment_pair(C fp, C fm, C& drho, C& Jx, C& Jy, C
 template <int EX, int EY, int N, bool FORCE, typename C>
 __device__ __forceinline__ void pair_update_ct(const CellCoef<C>& q, C omw, C omo, C& fp, C& fm) {
     const C s = lin<EX, EY>(q.utx, q.uty);
-    const C t = s * s;
+    const C t = mul_rn(s, s);
     C Ge = N >= 4 ? fma(t, fma(t, q.a2, q.a1), q.a0) : fma(t, q.a1, q.a0);
-    C Go = N >= 3 ? s * fma(t, q.b1, q.b0) : s * q.b0;
+    C Go = N >= 3 ? mul_rn(s, fma(t, q.b1, q.b0)) : mul_rn(s, q.b0);
     if constexpr (FORCE) {
         if constexpr (EX != 0) {
             // even: tau rho (g.xi) s; odd: (g.xi)(tau rho + (tau/2) Q)
@@ -301,9 +313,9 @@ __device__ __forceinline__ void pair_update_ct(const CellCoef<C>& q, C omw, C om
         }
         Go = Go - lin<EX, EY>(q.hx, q.hy);      // - tau (g.A).xi
     }
-    const C X = omw * Ge, Y = omw * Go;
-    fp = fma(omo, fp, X + Y);
-    fm = fma(omo, fm, X - Y);
+    const C X = mul_rn(omw, Ge);
+    fp = fma(omo, fp, fma(omw, Go, X));
+    fm = fma(omo, fm, fma(-omw, Go, X));
 }
 
 template <class SET, typename C, int... I>
@@ -492,9 +504,9 @@ k_step_warp(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* 
     if (node && p == 0 && k.R) f0 = value(0);
     const C sum = fp + fm, dif = fp - fm;
     const int pp = act ? p : 0;
-    C m[6] = {sum + f0, act ? k.pex[pp] * dif : C(0), act ? k.pey[pp] * dif : C(0),
-              act ? k.pexx[pp] * sum : C(0), act ? k.pexy2[pp] * sum : C(0),
-              act ? k.peyy[pp] * sum : C(0)};
+    C m[6] = {sum + f0, act ? mul_rn(k.pex[pp], dif) : C(0), act ? mul_rn(k.pey[pp], dif) : C(0),
+              act ? mul_rn(k.pexx[pp], sum) : C(0), act ? mul_rn(k.pexy2[pp], sum) : C(0),
+              act ? mul_rn(k.peyy[pp], sum) : C(0)};
 #pragma unroll
     for (int o = LP / 2; o > 0; o >>= 1)
 #pragma unroll

@@ -176,3 +176,93 @@ def test_config4_workload_runs():
     for s in slots:
         assert eng.info(s, status=True)[1] == 0
         assert res[s, 1] > 0 and np.isfinite(res[s, 1])
+
+
+# Channels for the resident-chunk path: x wrap by constant offset (Nx = 1),
+# by one compare (Nx >= max|e_x|) and by a modulo (1 < Nx < max|e_x|); the
+# narrowest channel (Ny = max|e_y|); the largest bundle entry (4096 nodes
+# would not fit 227 KB for D2V16 fp32, 2048 does); one over the node limit
+# (tiled in both engines); more small channels than one bundle holds.
+RESIDENT_MIX = ([("D2V16", 3, 1, 2048, 0.02), ("D2V16", 3, 1, 4, 0.5), ("D2V33", 4, 3, 21, 0.1),
+                 ("D2V32", 3, 5, 12, 0.3), ("D3V96xz", 3, 17, 14, 0.7), ("D2V33", 4, 64, 31, 0.05),
+                 ("D3V107xz", 3, 2, 19, 0.2), ("D2V16", 2, 1, 5000, 0.1), ("D2V33", 2, 1, 9, 1.0)]
+                + [("D2V16", 3, 1, 16 + (i % 7), 0.01 * (1 + i)) for i in range(70)])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_resident_chunks_bitwise_equal_tiled(precision):
+    """A whole chunk in shared memory (two-step in-place streaming, ghost
+    rows at the walls) gives bitwise the per-step tiled kernel's states,
+    observables and status, also after slots are removed and added."""
+    import paper_1510_08886_gb300 as lbm
+    engines = [lbm.Engine(precision, max_solves=96, arena_bytes=256 << 20, chunk=20,
+                          resident=r) for r in (True, False)]
+    slots = [[_add(eng, s, seed=11 + i) for i, s in enumerate(RESIDENT_MIX)] for eng in engines]
+    res = [eng.run(2).copy() for eng in engines]
+
+    def compare(live):
+        for i in live:
+            Nx, Ny = RESIDENT_MIX[i][2], RESIDENT_MIX[i][3]
+            ma = engines[0].moments(slots[0][i], Nx, Ny)
+            mb = engines[1].moments(slots[1][i], Nx, Ny)
+            for a, b in zip(ma, mb):
+                assert np.array_equal(a, b), (i, RESIDENT_MIX[i])
+            assert np.array_equal(res[0][slots[0][i]], res[1][slots[1][i]]), i
+            assert engines[0].info(slots[0][i], status=True) == engines[1].info(slots[1][i],
+                                                                                status=True)
+
+    live = list(range(len(RESIDENT_MIX)))
+    compare(live)
+    for eng, sl in zip(engines, slots):
+        for i in (0, 3, 20, 40):
+            eng.remove(sl[i])
+    live = [i for i in live if i not in (0, 3, 20, 40)]
+    extra = ("D2V33", 4, 7, 40, 0.08)
+    xs = [_add(eng, extra, seed=99) for eng in engines]
+    res = [eng.run(1).copy() for eng in engines]
+    compare(live)
+    for a, b in zip(engines[0].moments(xs[0], 7, 40), engines[1].moments(xs[1], 7, 40)):
+        assert np.array_equal(a, b)
+    for eng in engines:
+        eng.close()
+
+
+def test_resident_switch_validates():
+    import paper_1510_08886_gb300 as lbm
+    eng = lbm.Engine("fp32", max_solves=2, arena_bytes=16 << 20)
+    from paper_1510_08886_gb300 import _lib
+    assert _lib.lib().lbm_engine_set_resident(eng._h, 2) == _lib.LBM_EINVAL
+    eng.set_resident(False)
+    eng.set_resident(True)
+    eng.close()
+
+
+def test_engine_checkpoint_restores_bitwise():
+    """A slot's checkpoint restored into another engine's slot continues
+    bit-identically (fp32); a checkpoint of a different solve is refused."""
+    import paper_1510_08886_gb300 as lbm
+    from paper_1510_08886_gb300 import _lib
+    spec = ("D2V33", 4, 16, 24, 0.2)
+    a = lbm.Engine("fp32", max_solves=4, arena_bytes=64 << 20, chunk=10)
+    sa = _add(a, spec, seed=21)
+    a.run(3)
+    ck = a.get_state(sa)
+    a.run(2)
+    b = lbm.Engine("fp32", max_solves=4, arena_bytes=64 << 20, chunk=10, resident=False)
+    _add(b, MIX[1], seed=1)                   # another solve first: a different slot
+    sb = _add(b, spec, seed=99)                # different initial state, same solve
+    b.set_state(sb, ck)
+    assert b.info(sb)[0] == 30
+    b.run(2)
+    for x, y in zip(a.moments(sa, 16, 24), b.moments(sb, 16, 24)):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.get_state(sa)[64:], b.get_state(sb)[64:])
+    other = _add(b, ("D2V33", 4, 16, 25, 0.2), seed=3)
+    with pytest.raises(RuntimeError):
+        b.set_state(other, ck)
+    bad = ck.copy()
+    bad[:8] = 0
+    assert _lib.lib().lbm_engine_set_state(b._h, sb, bad.ctypes.data_as(_lib.ctypes.c_void_p),
+                                           bad.nbytes) == _lib.LBM_EINVAL
+    a.close()
+    b.close()
