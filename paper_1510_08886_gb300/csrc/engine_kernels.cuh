@@ -93,15 +93,15 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
                 const int y = cell / k.Nx;
                 const int x = cell - y * k.Nx;
                 const bool nb = y < k.maxey, nt = y >= k.Ny - k.maxey;
-                const double pb = nb ? wall_dpsi<S, C>(k, src, x, true) : 0.0;
-                const double pt = nt ? wall_dpsi<S, C>(k, src, x, false) : 0.0;
+                const C pb = nb ? wall_dpsi<S, C>(k, src, x, true) : C(0);
+                const C pt = nt ? wall_dpsi<S, C>(k, src, x, false) : C(0);
 #pragma unroll
                 for (int a = 0; a < V; ++a) {
                     const int ys = y - k.ey[a];
                     if (ys < 0)
-                        f[a] = C(pb * k.w[a]);
+                        f[a] = pb * k.cw[a];
                     else if (ys >= k.Ny)
-                        f[a] = C(pt * k.w[a]);
+                        f[a] = pt * k.cw[a];
                     else
                         f[a] = pull<S, C>(k, src, a, x, y);
                 }
@@ -203,10 +203,10 @@ __device__ __forceinline__ int xwrap(int x, int Nx) {
 // population b of node m = (x - e_x, j) sits at (m, bbar); in an A step it
 // sits in the ghost row at (m + e_b, b).
 template <typename S, typename C>
-__device__ __noinline__ double res_wall_dpsi(const KParams<C>& k, const S* sb, int PS, int G, int x,
-                                             bool bottom, bool stepA) {
+__device__ __noinline__ C res_wall_dpsi(const KParams<C>& k, const S* sb, int PS, int G, int x,
+                                        bool bottom, bool stepA) {
     const int Nx = k.Nx;
-    double acc = 0.0;
+    C acc = C(0);
     for (int b = k.R; b < k.V; ++b) {
         const int ey = k.ey[b];
         if (bottom ? (ey >= 0) : (ey <= 0)) continue;
@@ -218,7 +218,7 @@ __device__ __noinline__ double res_wall_dpsi(const KParams<C>& k, const S* sb, i
             const int row = bottom ? j : (k.Ny - 1 - j);
             const S v = stepA ? sb[(long long)b * PS + (long long)(row + ey + G) * Nx + x]
                               : sb[(long long)bb * PS + (long long)(row + G) * Nx + xs];
-            acc += (double)ld_pop<S, C>(k, v, b);
+            acc += ld_pop<S, C>(k, v, b);
         }
     }
     return acc * k.inv_den;
@@ -260,7 +260,7 @@ __device__ __forceinline__ void res_node(const EngineSolve<C>& B, S* sb, int slo
     const KParams<C>& k = B.k;
     const int Nx = k.Nx, Ny = k.Ny;
     const int PS = Nx * (Ny + 2 * G);
-    const int y = cell / Nx;
+    const int y = Nx == 1 ? cell : cell / Nx;     // one-column channels need no division
     const int x = cell - y * Nx;
     C f[V];
     const int mode = Nx == 1 ? 0 : (Nx >= k.maxex ? 1 : 2);
@@ -273,15 +273,15 @@ __device__ __forceinline__ void res_node(const EngineSolve<C>& B, S* sb, int slo
             res_pull<SET, S, C, 2, STEP_A>(k, sb, PS, x, y, f, std::make_integer_sequence<int, V>{});
     } else {
         const bool nb = y < G, nt = y >= Ny - G;
-        const double pb = nb ? res_wall_dpsi<S, C>(k, sb, PS, G, x, true, STEP_A) : 0.0;
-        const double pt = nt ? res_wall_dpsi<S, C>(k, sb, PS, G, x, false, STEP_A) : 0.0;
+        const C pb = nb ? res_wall_dpsi<S, C>(k, sb, PS, G, x, true, STEP_A) : C(0);
+        const C pt = nt ? res_wall_dpsi<S, C>(k, sb, PS, G, x, false, STEP_A) : C(0);
 #pragma unroll
         for (int a = 0; a < V; ++a) {
             const int ys = y - k.ey[a];
             if (ys < 0) {
-                f[a] = C(pb * k.w[a]);
+                f[a] = pb * k.cw[a];
             } else if (ys >= Ny) {
-                f[a] = C(pt * k.w[a]);
+                f[a] = pt * k.cw[a];
             } else if (STEP_A) {
                 f[a] = ld_pop<S, C>(k, sb[(long long)a * PS + (long long)(y + G) * Nx + x], a);
             } else {
@@ -363,7 +363,7 @@ k_engine_resident(const EngineSolve<C>* __restrict__ solves, const ResBundle* __
             if (cell >= ch.ncell) continue;
             const EngineSolve<C>& B = solves[ch.slot];
             const int Nx = B.k.Nx, PS = Nx * (B.k.Ny + 2 * G);
-            const int y = cell / Nx, x = cell - y * Nx;
+            const int y = Nx == 1 ? cell : cell / Nx, x = cell - y * Nx;
             const S* src = static_cast<const S*>(B.f[B.phase]);
             S* sb = sm + ch.off;
 #pragma unroll
@@ -403,7 +403,7 @@ k_engine_resident(const EngineSolve<C>* __restrict__ solves, const ResBundle* __
             if (cell >= ch.ncell) continue;
             const EngineSolve<C>& B = solves[ch.slot];
             const int Nx = B.k.Nx, PS = Nx * (B.k.Ny + 2 * G);
-            const int y = cell / Nx, x = cell - y * Nx;
+            const int y = Nx == 1 ? cell : cell / Nx, x = cell - y * Nx;
             S* dst = static_cast<S*>(B.f[B.phase]);
             const S* sb = sm + ch.off;
 #pragma unroll

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <queue>
 #include <vector>
 
 #include "engine_launch.cuh"
@@ -207,19 +208,86 @@ bool res_eligible(lbm_engine* e, const EngSlot& sl) {
            ((n + 31) & ~size_t(31)) <= size_t(lbm::kResNodes) && res_occupancy(e, sl.group) > 0;
 }
 
-// Work lists: per group, bundles of resident channels (first-fit decreasing by
-// shared-memory footprint, largest bundles first) and tiles of the others.
+struct Bin {
+    size_t bytes = 0;
+    int nodes = 0;
+    std::vector<int> members;
+};
+
+struct ResItem {
+    size_t bytes;
+    int nodes;     // padded to 32
+    int slot;
+};
+
+// Pack resident channels into bundles for `grid` persistent blocks: the
+// fewest whole waves (bundles = waves x grid) whose bundles respect the
+// shared-memory, node and channel limits, the channels placed largest first
+// on the least-loaded bundle (by nodes), so that every block gets about the
+// same work.  Bundles are returned largest first (the blocks take them in
+// that order).
+std::vector<Bin> pack_bundles(std::vector<ResItem> items, size_t capb, int grid) {
+    std::vector<Bin> out;
+    if (items.empty()) return out;
+    std::stable_sort(items.begin(), items.end(),
+                     [](const ResItem& a, const ResItem& b) { return a.nodes > b.nodes; });
+    size_t total_b = 0, total_n = 0;
+    for (const ResItem& it : items) {
+        total_b += it.bytes;
+        total_n += size_t(it.nodes);
+    }
+    const size_t per_wave_b = capb * size_t(grid), per_wave_n = size_t(lbm::kResNodes) * grid;
+    size_t waves = std::max<size_t>(1, std::max((total_b + per_wave_b - 1) / per_wave_b,
+                                                (total_n + per_wave_n - 1) / per_wave_n));
+    using Load = std::pair<long long, int>;   // (nodes, bundle)
+    for (;; ++waves) {
+        const size_t nb = std::min(items.size(), waves * size_t(grid));
+        std::vector<Bin> bins(nb);
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+        for (size_t i = 0; i < nb; ++i) heap.push({0, int(i)});
+        std::vector<Load> skipped;
+        bool ok = true;
+        for (const ResItem& it : items) {
+            bool placed = false;
+            skipped.clear();
+            while (!heap.empty()) {
+                const Load top = heap.top();
+                heap.pop();
+                Bin& b = bins[top.second];
+                if (b.bytes + it.bytes <= capb && b.nodes + it.nodes <= lbm::kResNodes &&
+                    int(b.members.size()) < lbm::kResMaxCh) {
+                    b.bytes += it.bytes;
+                    b.nodes += it.nodes;
+                    b.members.push_back(it.slot);
+                    heap.push({b.nodes, top.second});
+                    placed = true;
+                    break;
+                }
+                skipped.push_back(top);
+            }
+            for (const Load& l : skipped) heap.push(l);
+            if (!placed) {
+                ok = false;
+                break;
+            }
+        }
+        if (!ok) continue;
+        for (Bin& b : bins)
+            if (!b.members.empty()) out.push_back(std::move(b));
+        std::stable_sort(out.begin(), out.end(),
+                         [](const Bin& a, const Bin& b) { return a.nodes > b.nodes; });
+        return out;
+    }
+}
+
+// Work lists: per group, bundles of resident channels (pack_bundles) and
+// tiles of the others.
 int rebuild_tiles(lbm_engine* e) {
     std::vector<lbm::EngineTile> t;
     std::vector<lbm::ResBundle> bundles;
     std::vector<lbm::ResChannel> chans;
     std::vector<GroupWork> plan;
     std::vector<int> counts(2 * kGroups, 0), nbund(2 * kGroups, 0);   // count, offset
-    struct Bin {
-        size_t bytes;
-        int nodes;
-        std::vector<int> members;
-    };
     for (int g = 0; g < kGroups; ++g) {
         const size_t start = t.size(), bstart = bundles.size();
         std::vector<int> res;
@@ -233,30 +301,12 @@ int rebuild_tiles(lbm_engine* e) {
             const int n = sl.spec.Nx * sl.spec.Ny;
             for (int c0 = 0; c0 < n; c0 += lbm::kBlock) t.push_back({s, c0});
         }
-        std::stable_sort(res.begin(), res.end(), [&](int a, int b) {
-            return res_bytes(e->slots[a].spec) > res_bytes(e->slots[b].spec);
-        });
-        std::vector<Bin> bins;
-        for (int s : res) {
-            const size_t by = res_bytes(e->slots[s].spec);
-            const int nd = (e->slots[s].spec.Nx * e->slots[s].spec.Ny + 31) & ~31;
-            Bin* dst = nullptr;
-            for (Bin& b : bins)
-                if (b.bytes + by <= e->res_smem && b.nodes + nd <= lbm::kResNodes &&
-                    int(b.members.size()) < lbm::kResMaxCh) {
-                    dst = &b;
-                    break;
-                }
-            if (!dst) {
-                bins.push_back(Bin{0, 0, {}});
-                dst = &bins.back();
-            }
-            dst->bytes += by;
-            dst->nodes += nd;
-            dst->members.push_back(s);
-        }
-        std::stable_sort(bins.begin(), bins.end(),
-                         [](const Bin& a, const Bin& b) { return a.bytes > b.bytes; });
+        std::vector<ResItem> items;
+        for (int s : res)
+            items.push_back({res_bytes(e->slots[s].spec),
+                             (e->slots[s].spec.Nx * e->slots[s].spec.Ny + 31) & ~31, s});
+        const int rgrid = res.empty() ? 1 : std::max(1, res_occupancy(e, g)) * e->sms;
+        const std::vector<Bin> bins = pack_bundles(std::move(items), e->res_smem, rgrid);
         for (const Bin& b : bins) {
             lbm::ResBundle rb{int(chans.size()), int(b.members.size()), 0, 0};
             int off = 0;
