@@ -13,7 +13,12 @@ Plain numpy restatements, in fp64, of:
   n.xi > 0 (Eq. Wscalar, wallQuad), the wall errors sigma (Eq. wallError),
   sigma_Sigma (Eq. sigmaSigma) and the wall accuracy index Lambda_index
   (Eq. defbin) over the non-trivial moments of Eq. nontriv,
-* the (x, z) marginal of a 3D DVM for a channel that is uniform along y.
+* the (x, z) marginal of a 3D DVM for a channel that is uniform along y,
+* the weight solver of Sect. III: the matrix K(S) of Eq. defK built with the
+  scalar-product recurrence of the Hermite tensors printed below it, its null
+  space (Eq. defQua, dimker), the lattice speed c* at which a stencil becomes
+  a minimal DVM, and the wall augmentation of Sect. IV (Eq. 9.13, wallEq,
+  defA).
 """
 import itertools
 import math
@@ -185,3 +190,247 @@ def dvm2d(name, tables):
     if e.shape[1] != 2:
         raise ValueError(f"{name} is not two-dimensional")
     return e, w, c
+
+
+# ---- weight solver (Sect. III) and wall augmentation (Sect. IV) -------------
+
+def hermite_product_polys(Q):
+    """P_m(a, b, s) = H^(m)(xi) . H^(m)(eta) (all indices contracted) as
+    polynomials in a = xi.xi, b = eta.eta, s = xi.eta, for m = 0..Q, from the
+    recurrence below Eq. defK:
+        P_{m+1} = (xi.eta - xi.d_eta - eta.d_xi + d_xi.d_eta) P_m.
+    With f = f(a, b, s): d_xi_i f = 2 xi_i f_a + eta_i f_s and
+    d_eta_i f = 2 eta_i f_b + xi_i f_s, hence
+        xi.d_eta f  = 2 s f_b + a f_s,      eta.d_xi f = 2 s f_a + b f_s,
+        d_xi.d_eta f = 4 s f_ab + 2 b f_bs + 2 a f_as + s f_ss + D f_s.
+    The dimension D enters, so polynomials are returned as functions of D:
+    a list of dicts {(i, j, k, l): coeff} meaning coeff a^i b^j s^k D^l."""
+    def add(out, key, v):
+        if v:
+            out[key] = out.get(key, 0) + v
+
+    P = [{(0, 0, 0, 0): 1}]
+    for _ in range(Q):
+        cur, nxt = P[-1], {}
+        for (i, j, k, l), v in cur.items():
+            add(nxt, (i, j, k + 1, l), v)                      # s P
+            if j:
+                add(nxt, (i, j - 1, k + 1, l), -2 * j * v)     # -2 s P_b
+            if k:
+                add(nxt, (i + 1, j, k - 1, l), -k * v)         # -a P_s
+            if i:
+                add(nxt, (i - 1, j, k + 1, l), -2 * i * v)     # -2 s P_a
+            if k:
+                add(nxt, (i, j + 1, k - 1, l), -k * v)         # -b P_s
+            if i and j:
+                add(nxt, (i - 1, j - 1, k + 1, l), 4 * i * j * v)      # 4 s P_ab
+            if j and k:
+                add(nxt, (i, j, k - 1, l), 2 * j * k * v)              # 2 b P_bs
+            if i and k:
+                add(nxt, (i, j, k - 1, l), 2 * i * k * v)              # 2 a P_as
+            if k >= 2:
+                add(nxt, (i, j, k - 1, l), k * (k - 1) * v)            # s P_ss
+            if k:
+                add(nxt, (i, j, k - 1, l + 1), k * v)                  # D P_s
+        P.append({key: v for key, v in nxt.items() if v})
+    return P
+
+
+def kmatrix_orders(e, c, Q):
+    """The Q blocks K^(m)_{ab} = H^(m)(xi_a) . H^(m)(xi_b), m = 1..Q, whose
+    sum is K(S) of Eq. defK; xi = c e."""
+    xi = c * np.asarray(e, dtype=np.float64)
+    D = xi.shape[1]
+    a = np.sum(xi * xi, axis=1)
+    A, B = np.meshgrid(a, a, indexing="ij")
+    S = xi @ xi.T
+    out = []
+    for poly in hermite_product_polys(Q)[1:]:
+        K = np.zeros_like(S)
+        for (i, j, k, l), v in poly.items():
+            K += v * A ** i * B ** j * S ** k * float(D) ** l
+        out.append(K)
+    return out
+
+
+def kmatrix(e, c, Q):
+    """K(S) of Eq. defK."""
+    return sum(kmatrix_orders(e, c, Q))
+
+
+def symmetry_groups(e):
+    """Group index of each velocity (Eq. wdach): velocities related by the
+    lattice reflections (component permutations and sign flips) share the
+    multiset of absolute components.  Groups are numbered in order of first
+    appearance; raises if an orbit is incomplete."""
+    keys, gid = {}, []
+    for row in np.asarray(e).tolist():
+        key = tuple(sorted(abs(x) for x in row))
+        gid.append(keys.setdefault(key, len(keys)))
+    gid = np.array(gid)
+    for key, g in keys.items():
+        orbit = set()
+        for perm in itertools.permutations(key):
+            for signs in itertools.product((1, -1), repeat=len(key)):
+                orbit.add(tuple(sg * p for sg, p in zip(signs, perm)))
+        if int(np.sum(gid == g)) != len(orbit):
+            raise ValueError(f"incomplete symmetry group {key}")
+    return gid
+
+
+def reduced_kmatrix(e, c, Q):
+    """K reduced to one unknown per symmetry group (weights equal within a
+    group, Eq. wdach): Kg = G^T (sum_m K^(m) / max|K^(m)|) G with G the
+    velocity-group incidence matrix.  Scaling each order by a positive
+    factor leaves the null space unchanged, because w.K.w is the sum over m
+    of the squared Hermite moments (the argument below Eq. defK), so w is in
+    the null space exactly when every order's moment vanishes."""
+    gid = symmetry_groups(e)
+    Gm = np.zeros((len(gid), gid.max() + 1))
+    Gm[np.arange(len(gid)), gid] = 1.0
+    K = np.zeros((len(gid), len(gid)))
+    for Km in kmatrix_orders(e, c, Q):
+        scale = np.max(np.abs(Km))
+        if scale > 0:
+            K += Km / scale
+    return Gm.T @ K @ Gm, gid
+
+
+def null_space(e, c, Q, rtol=1e-12):
+    """Null space of the reduced K: (basis of group weight vectors as
+    columns, eigenvalues ascending, group index of each velocity).  The
+    matrix is first equilibrated, Kh = d^-1/2 Kg d^-1/2 with d = diag(Kg)
+    (a change of unknowns W = d^-1/2 Wh, so the null spaces correspond); the
+    nullity (Eq. dimker) is the number of eigenvalues of Kh below rtol times
+    the largest."""
+    Kg, gid = reduced_kmatrix(e, c, Q)
+    dh = 1.0 / np.sqrt(np.diag(Kg))
+    lam, vec = np.linalg.eigh(dh[:, None] * Kg * dh[None, :])
+    n = int(np.sum(lam < rtol * lam[-1]))
+    return dh[:, None] * vec[:, :n], lam, gid
+
+
+def solve_weights(e, c, Q):
+    """Weights of a stencil (Eq. defQua): the normalised (sum w = 1) null
+    vector of K when dim ker K = 1.  Returns (w, nullity)."""
+    basis, _, gid = null_space(e, c, Q)
+    n = basis.shape[1]
+    if n != 1:
+        return None, n
+    wg = basis[:, 0]
+    w = wg[gid]
+    return w / np.sum(w), 1
+
+
+def hermite_1d(n, x):
+    """Probabilists' Hermite polynomial He_n(x): He_0 = 1, He_1 = x,
+    He_{k+1} = x He_k - k He_{k-1}."""
+    h0, h1 = np.ones_like(x), x
+    if n == 0:
+        return h0
+    for k in range(1, n):
+        h0, h1 = h1, x * h1 - k * h0
+    return h1
+
+
+def multi_indices(D, m):
+    """Exponent tuples (n_1..n_D), sum m: the distinct components of a
+    symmetric rank-m tensor in D dimensions."""
+    return [t for t in itertools.product(range(m + 1), repeat=D) if sum(t) == m]
+
+
+def moment_matrix(e, c, Q):
+    """The orthogonality conditions of Eq. orth with n = 0, written per
+    symmetry group: row (m, n_1..n_D), column g holds
+    sum_{a in g} H^(m)_{n}(xi_a), where the Hermite tensor component with
+    n_d indices equal to d is prod_d He_{n_d}(xi_d) (the Gaussian weight
+    factorises over the components).  Each order m is scaled by the norm of
+    the same sums taken over absolute values, so that rows that vanish by
+    symmetry stay at rounding level.  Returns (M, group index)."""
+    gid = symmetry_groups(e)
+    G = gid.max() + 1
+    xi = c * np.asarray(e, dtype=np.float64)
+    D = xi.shape[1]
+    He = [[hermite_1d(n, xi[:, d]) for n in range(Q + 1)] for d in range(D)]
+    blocks = []
+    for m in range(1, Q + 1):
+        rows, arows = [], []
+        for t in multi_indices(D, m):
+            v = np.prod([He[d][t[d]] for d in range(D)], axis=0)
+            rows.append(np.bincount(gid, weights=v, minlength=G))
+            arows.append(np.bincount(gid, weights=np.abs(v), minlength=G))
+        A, Aa = np.array(rows), np.array(arows)
+        scale = np.linalg.norm(Aa)
+        if scale > 0:
+            blocks.append(A / scale)
+    return np.vstack(blocks), gid
+
+
+def orth_gap(e, c, Q):
+    """Smallest over largest singular value of the moment matrix with
+    unit-norm columns: zero where the stencil admits weights of order Q
+    (c = c*), linear in |c - c*| near it."""
+    M, _ = moment_matrix(e, c, Q)
+    M = M / np.linalg.norm(M, axis=0)
+    s = np.linalg.svd(M, compute_uv=False)
+    return s[-1] / s[0]
+
+
+def find_c(e, Q, c_lo, c_hi, n_scan=400):
+    """Lattice speed c* in [c_lo, c_hi] at which the stencil is a minimal DVM
+    of order Q (dim ker K = 1) with positive weights: scan orth_gap for local
+    minima, refine each by golden-section search (the gap has a kink at c*),
+    and return the smallest c* whose weights are all positive, or None."""
+    cs = np.linspace(c_lo, c_hi, n_scan)
+    f = np.array([orth_gap(e, c, Q) for c in cs])
+    phi = (math.sqrt(5.0) - 1.0) / 2.0
+    for i in range(1, n_scan - 1):
+        if not (f[i] <= f[i - 1] and f[i] <= f[i + 1]):
+            continue
+        lo, hi = cs[i - 1], cs[i + 1]
+        x1, x2 = hi - phi * (hi - lo), lo + phi * (hi - lo)
+        f1, f2 = orth_gap(e, x1, Q), orth_gap(e, x2, Q)
+        while hi - lo > 4e-16 * hi:
+            if f1 <= f2:
+                hi, x2, f2 = x2, x1, f1
+                x1 = hi - phi * (hi - lo)
+                f1 = orth_gap(e, x1, Q)
+            else:
+                lo, x1, f1 = x1, x2, f2
+                x2 = lo + phi * (hi - lo)
+                f2 = orth_gap(e, x2, Q)
+        c = 0.5 * (lo + hi)
+        if orth_gap(e, c, Q) > 1e-9:
+            continue
+        w, n = solve_weights(e, c, Q)
+        if n == 1 and np.all(w > 0):
+            return float(c)
+    return None
+
+
+def augment(e, c, Q, constraints):
+    """Wall-augmented weights (Sect. IV): w = x_j w^(j) over an orthogonal
+    basis of the null space of K (Eq. 9.13), x from the equations of
+    Eq. wallEq, A_kj = sum_{n.xi_a > 0} T^a_k w^(j)_a (Eq. defA) with
+    b_k = W_k (Eq. Wscalar), for the selected non-trivial wall moments
+    (indices into nontrivial_moments(D, Q)), together with sum w = 1;
+    least squares when overdetermined.  Returns (w, residual norm)."""
+    basis, _, gid = null_space(e, c, Q)
+    if basis.shape[1] == 0:
+        raise ValueError("K(S) is regular at this c")
+    xi = c * np.asarray(e, dtype=np.float64)
+    D = xi.shape[1]
+    moms = nontrivial_moments(D, Q)
+    Wb = basis[gid, :]                        # velocity weights of each basis vector
+    up = xi[:, -1] > 0
+    rows, rhs = [], []
+    for k in constraints:
+        mx, my, mz = moms[k]
+        T = xi[:, 0] ** mx * (xi[:, 1] ** my if D == 3 else 1.0) * xi[:, -1] ** mz
+        rows.append(T[up] @ Wb[up])
+        rhs.append(wall_moment_exact(D, mx, my, mz))
+    rows.append(np.sum(Wb, axis=0))
+    rhs.append(1.0)
+    A, b = np.array(rows), np.array(rhs)
+    x, *_ = np.linalg.lstsq(A, b, rcond=None)
+    return Wb @ x, float(np.linalg.norm(A @ x - b))
