@@ -97,6 +97,45 @@ int lbm_dvm_marginal_xz(int V3, const int* e3, const double* w3, int cap,
  * Gaussian moment (i-1)!!(j-1)!! (relative tolerance 1e-9). */
 int lbm_dvm_quadrature_order(const lbm_dvm* dvm, int* Q_out);
 
+/* ---- DVM generator (host only, no GPU needed) ---------------------------- */
+/* Velocities: e[V*D] ints, row-major, D = 2 (x, z) or 3 (x, y, z), the last
+ * component the wall normal; multiples of the lattice speed c.  The stencil
+ * must be closed under the lattice reflections (component permutations and
+ * sign flips), else LBM_EINVAL.  1 <= Q <= 16. */
+
+/* Weights of a stencil (Sect. III): the normalised (sum w = 1) null vector
+ * of K(S) (Eq. defQua, defK), one weight per symmetry group (Eq. wdach).
+ * *nullity_out = dim ker K (Eq. dimker): 1 for a DVM of order Q at this c
+ * (weights in w_out[V]); 0 when K(S) is regular (c is not a c*); > 1 when
+ * the weights are not unique (see lbm_dvm_augment).  w_out is NaN unless
+ * the nullity is 1.  Null directions: singular values of the per-group
+ * orthogonality conditions below 1e-9 of the largest. */
+int lbm_dvm_solve_weights(int D, int V, const int* e, double c, int Q, double* w_out,
+                          int* nullity_out);
+
+/* Lattice speed c* in [c_lo, c_hi] at which the stencil is a minimal DVM
+ * of order Q (dim ker K = 1) with positive weights (Eq. dimker): the
+ * smallest such c*, located to rounding (400-point scan, golden-section
+ * refinement).  LBM_ENOTCONV if there is none in the interval. */
+int lbm_dvm_find_c(int D, int V, const int* e, int Q, double c_lo, double c_hi,
+                   double* c_out);
+
+/* The L non-trivial equilibrium wall moments (m_x, m_y, m_z) of Eq. nontriv
+ * in the paper's order (increasing n, decreasing m_z, decreasing m_x;
+ * m_y = 0 in 2D), 3 ints each into m_out (cap moments; NULL with cap 0
+ * returns only *L_out). */
+int lbm_dvm_nontrivial_moments(int D, int Q, int cap, int* m_out, int* L_out);
+
+/* Wall-augmented weights (Sect. IV): w = x_j w^(j) over a basis of the null
+ * space of K(S) (Eq. 9.13), x from A x = b (Eq. wallEq, defA) for the nk
+ * selected non-trivial wall moments k[] (indices into
+ * lbm_dvm_nontrivial_moments), b their exact values (Eq. Wscalar), together
+ * with sum w = 1; least squares when overdetermined, minimum norm when
+ * underdetermined.  w_out[V]; *residual_out (may be NULL) = |A x - b|.
+ * LBM_EDEGREE if K(S) is regular at c. */
+int lbm_dvm_augment(int D, int V, const int* e, double c, int Q, int nk, const int* k,
+                    double* w_out, double* residual_out);
+
 /* ---- solver lifetime ---------------------------------------------------- */
 
 /* Device bytes lbm_create_in needs for this problem (both population

@@ -20,7 +20,8 @@ from . import _lib
 from ._lib import LBMError, check, lbm_dvm
 
 __all__ = ["dvm", "dvm_from_groups", "Solver", "LBMError", "force_for_mach", "tau_of_kn",
-           "quadrature_order"]
+           "quadrature_order", "dvm_weights", "dvm_find_c", "dvm_nontrivial_moments",
+           "dvm_augment", "Engine"]
 
 PRECISIONS = {"fp64": _lib.LBM_FP64, "fp32": _lib.LBM_FP32, "fp16": _lib.LBM_FP16,
               "bf16": _lib.LBM_BF16}
@@ -101,6 +102,60 @@ def quadrature_order(e, w, c):
     Q = ctypes.c_int(-1)
     check(_lib.lib().lbm_dvm_quadrature_order(d.ref(), ctypes.byref(Q)))
     return Q.value
+
+
+def _stencil(e):
+    e = np.ascontiguousarray(np.asarray(e), dtype=np.int32)
+    if e.ndim != 2 or e.shape[1] not in (2, 3):
+        raise ValueError("velocities must be an (V, 2) or (V, 3) integer array")
+    return e, e.shape[1], e.shape[0]
+
+
+def dvm_weights(e, c, Q):
+    """Weights of a stencil from its velocities (Sect. III, Eq. defQua,
+    defK): returns (w, nullity); w is None unless dim ker K = 1."""
+    e, D, V = _stencil(e)
+    w = np.empty(V)
+    n = ctypes.c_int(-1)
+    check(_lib.lib().lbm_dvm_solve_weights(D, V, _ip(e), float(c), int(Q), _dp(w), ctypes.byref(n)),
+          "lbm_dvm_solve_weights")
+    return (w if n.value == 1 else None), n.value
+
+
+def dvm_find_c(e, Q, c_lo, c_hi):
+    """Lattice speed c* in [c_lo, c_hi] of a minimal DVM of order Q with
+    positive weights (Eq. dimker), or None."""
+    e, D, V = _stencil(e)
+    c = ctypes.c_double(0.0)
+    rc = _lib.lib().lbm_dvm_find_c(D, V, _ip(e), int(Q), float(c_lo), float(c_hi), ctypes.byref(c))
+    if rc == _lib.LBM_ENOTCONV:
+        return None
+    check(rc, "lbm_dvm_find_c")
+    return c.value
+
+
+def dvm_nontrivial_moments(D, Q):
+    """Exponents (m_x, m_y, m_z) of the non-trivial wall moments (Eq. nontriv)."""
+    L = ctypes.c_int(0)
+    check(_lib.lib().lbm_dvm_nontrivial_moments(int(D), int(Q), 0, None, ctypes.byref(L)))
+    out = np.zeros(3 * max(L.value, 1), dtype=np.int32)
+    check(_lib.lib().lbm_dvm_nontrivial_moments(int(D), int(Q), L.value, _ip(out), ctypes.byref(L)),
+          "lbm_dvm_nontrivial_moments")
+    return [tuple(int(x) for x in out[3 * k:3 * k + 3]) for k in range(L.value)]
+
+
+def dvm_augment(e, c, Q, constraints):
+    """Wall-augmented weights (Sect. IV, Eq. 9.13, wallEq, defA) imposing the
+    selected non-trivial wall moments (indices into dvm_nontrivial_moments)
+    and sum w = 1.  Returns (w, residual)."""
+    e, D, V = _stencil(e)
+    k = np.ascontiguousarray(constraints, dtype=np.int32)
+    w = np.empty(V)
+    r = ctypes.c_double(0.0)
+    check(_lib.lib().lbm_dvm_augment(D, V, _ip(e), float(c), int(Q), len(k),
+                                     _ip(k) if len(k) else None, _dp(w), ctypes.byref(r)),
+          "lbm_dvm_augment")
+    return w, r.value
 
 
 def _torch_cuda():

@@ -30,6 +30,15 @@ SIGNATURES = {
     "lbm_dvm_marginal_xz": (ctypes.c_int, [ctypes.c_int, c_int_p, c_double_p, ctypes.c_int,
                                            c_int_p, c_double_p, c_int_p]),
     "lbm_dvm_quadrature_order": (ctypes.c_int, [ctypes.POINTER(lbm_dvm), c_int_p]),
+    "lbm_dvm_solve_weights": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, ctypes.c_double,
+                                             ctypes.c_int, c_double_p, c_int_p]),
+    "lbm_dvm_find_c": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, c_double_p]),
+    "lbm_dvm_nontrivial_moments": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, c_int_p,
+                                                  c_int_p]),
+    "lbm_dvm_augment": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, c_int_p, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_int, c_int_p, c_double_p,
+                                       c_double_p]),
     "lbm_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(lbm_dvm), ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, c_size_p]),
     "lbm_create": (ctypes.c_int, [ctypes.POINTER(lbm_dvm), ctypes.c_int, ctypes.c_int,
