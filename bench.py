@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-config1", action="store_true")
+    p.add_argument("--no-dvm-generator", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=8.0)
     p.add_argument("--serve-saturated-only", action="store_true",
                    help="serving section: only the saturated-capacity run")
@@ -224,6 +225,51 @@ def torch_stream():
     return torch.cuda.Stream()
 
 
+def dvm_generator_section(lbm, with_oracle=True):
+    """Host-side DVM generator (Sect. III-IV): from the velocities of every
+    printed stencil alone, the lattice speed c* (scan [0.8 c, 1.2 c]) and the
+    weights, or the W_zxx-augmented weights of the two augmented S3 sets;
+    errors against the printed values and the time taken by the library and,
+    on a subset, by the oracle."""
+    from lbm_inputs import DVM_TABLES, TEXTBOOK_TABLES
+    tables = {**DVM_TABLES, **TEXTBOOK_TABLES}
+    augmented = ("D3V77", "D3V107")
+    worst_c = worst_w = 0.0
+    t_lib = 0.0
+    for name, t in tables.items():
+        e, w, c = lbm.dvm_from_groups(t)
+        t0 = time.perf_counter()
+        if name in augmented:
+            k = [lbm.dvm_nontrivial_moments(3, t["Q"]).index((2, 0, 1))]
+            ws, _ = lbm.dvm_augment(e, c, t["Q"], k)
+        else:
+            cs = lbm.dvm_find_c(e, t["Q"], 0.8 * c, 1.2 * c)
+            ws, _ = lbm.dvm_weights(e, cs, t["Q"])
+            worst_c = max(worst_c, abs(cs / c - 1))
+        t_lib += time.perf_counter() - t0
+        worst_w = max(worst_w, float(np.max(np.abs(ws / w - 1))))
+    out = {"stencils": len(tables), "library_s": t_lib,
+           "max_rel_err_c_vs_printed": worst_c, "max_rel_err_w_vs_printed": worst_w}
+    if with_oracle:
+        import oracle.dvm as odvm
+        subset = ("D2V16", "D2V33", "D3V15", "D2Q9", "D3Q19")
+        t0 = time.perf_counter()
+        for name in subset:
+            e, _, c = odvm.expand(tables[name])
+            cs = odvm.find_c(e, tables[name]["Q"], 0.8 * c, 1.2 * c)
+            odvm.solve_weights(e, cs, tables[name]["Q"])
+        t_or = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for name in subset:
+            e, _, c = lbm.dvm_from_groups(tables[name])
+            lbm.dvm_weights(e, lbm.dvm_find_c(e, tables[name]["Q"], 0.8 * c, 1.2 * c),
+                            tables[name]["Q"])
+        out["subset"] = list(subset)
+        out["subset_library_s"] = time.perf_counter() - t0
+        out["subset_oracle_s"] = t_or
+    return out
+
+
 def config1_section(lbm):
     """Config 1: D2V16, N=3, Nx=1 x Ny=64, Kn=0.1, Ma 1e-3, rho=1, run until
     max|du| < 1e-10 tested every 100 steps (<= 50k steps): wall time to steady
@@ -376,6 +422,7 @@ def main():
     dist = replicas.init("nccl", torch.device("cuda", local))
     if ws > 1:      # scaling runs time the headline workload only
         args.no_variants = args.no_batched = args.no_serving = True
+        args.no_dvm_generator = True
 
     import __graft_entry__
     __graft_entry__.build_library()
@@ -496,6 +543,8 @@ def main():
     serving = None if args.no_serving else serving_section(lbm, args.serve_seconds,
                                                            args.serve_saturated_only)
     config1 = None if (args.no_config1 or ws > 1) else config1_section(lbm)
+    dvmgen = None if (args.no_dvm_generator or rank != 0) else dvm_generator_section(
+        lbm, with_oracle=not args.no_cpu_baseline)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -530,6 +579,7 @@ def main():
             "batched": batched,
             "serving": serving,
             "config1": config1,
+            "dvm_generator": dvmgen,
         }))
     if dist:
         dist.destroy_process_group()
