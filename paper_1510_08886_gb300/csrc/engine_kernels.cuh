@@ -93,8 +93,8 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
                 const int y = cell / k.Nx;
                 const int x = cell - y * k.Nx;
                 const bool nb = y < k.maxey, nt = y >= k.Ny - k.maxey;
-                const C pb = nb ? wall_dpsi<S, C>(k, src, x, true) : C(0);
-                const C pt = nt ? wall_dpsi<S, C>(k, src, x, false) : C(0);
+                const C pb = nb ? C(wall_dpsi<S, C>(k, src, x, true)) : C(0);
+                const C pt = nt ? C(wall_dpsi<S, C>(k, src, x, false)) : C(0);
 #pragma unroll
                 for (int a = 0; a < V; ++a) {
                     const int ys = y - k.ey[a];
@@ -203,10 +203,10 @@ __device__ __forceinline__ int xwrap(int x, int Nx) {
 // population b of node m = (x - e_x, j) sits at (m, bbar); in an A step it
 // sits in the ghost row at (m + e_b, b).
 template <typename S, typename C>
-__device__ __noinline__ C res_wall_dpsi(const KParams<C>& k, const S* sb, int PS, int G, int x,
+__device__ __noinline__ double res_wall_dpsi(const KParams<C>& k, const S* sb, int PS, int G, int x,
                                         bool bottom, bool stepA) {
     const int Nx = k.Nx;
-    C acc = C(0);
+    double acc = 0.0;
     for (int b = k.R; b < k.V; ++b) {
         const int ey = k.ey[b];
         if (bottom ? (ey >= 0) : (ey <= 0)) continue;
@@ -218,7 +218,7 @@ __device__ __noinline__ C res_wall_dpsi(const KParams<C>& k, const S* sb, int PS
             const int row = bottom ? j : (k.Ny - 1 - j);
             const S v = stepA ? sb[(long long)b * PS + (long long)(row + ey + G) * Nx + x]
                               : sb[(long long)bb * PS + (long long)(row + G) * Nx + xs];
-            acc += ld_pop<S, C>(k, v, b);
+            acc += (double)ld_pop<S, C>(k, v, b);
         }
     }
     return acc * k.inv_den;
@@ -273,8 +273,8 @@ __device__ __forceinline__ void res_node(const EngineSolve<C>& B, S* sb, int slo
             res_pull<SET, S, C, 2, STEP_A>(k, sb, PS, x, y, f, std::make_integer_sequence<int, V>{});
     } else {
         const bool nb = y < G, nt = y >= Ny - G;
-        const C pb = nb ? res_wall_dpsi<S, C>(k, sb, PS, G, x, true, STEP_A) : C(0);
-        const C pt = nt ? res_wall_dpsi<S, C>(k, sb, PS, G, x, false, STEP_A) : C(0);
+        const C pb = nb ? C(res_wall_dpsi<S, C>(k, sb, PS, G, x, true, STEP_A)) : C(0);
+        const C pt = nt ? C(res_wall_dpsi<S, C>(k, sb, PS, G, x, false, STEP_A)) : C(0);
 #pragma unroll
         for (int a = 0; a < V; ++a) {
             const int ys = y - k.ey[a];

@@ -194,7 +194,7 @@ void fill_params_impl(const lbm::SolveSpec* s, KParams<C>& k) {
         k.sw[a] = C(s->w[a] * s->scale);
         k.isw[a] = C(1.0 / (s->w[a] * s->scale));
     }
-    k.inv_den = C(1.0 / s->den);
+    k.inv_den = 1.0 / s->den;
     for (int p = 0; p < s->P; ++p) {
         const int a = s->R + p;
         const double x = s->ex[a], y = s->ey[a];

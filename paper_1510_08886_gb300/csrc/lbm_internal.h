@@ -56,7 +56,7 @@ struct KParams {
     // 16-bit storage only: stored h_a = d_a / (w_a S), S a per-solve power of 2
     C sw[LBM_MAX_V];             // w_a S      (load:  d = h * sw)
     C isw[LBM_MAX_V];            // 1/(w_a S)  (store: h = d * isw)
-    C inv_den;                   // 1 / sum_{e_y > 0} e_y w  (= same for e_y < 0)
+    double inv_den;              // 1 / sum_{e_y > 0} e_y w  (= same for e_y < 0)
     // per pair p, positive member e = (ex, ey):
     C pex[kMaxPairs], pey[kMaxPairs];
     C pexx[kMaxPairs], pexy2[kMaxPairs], peyy[kMaxPairs];   // ex^2, 2 ex ey, ey^2

@@ -110,13 +110,12 @@ __device__ __forceinline__ S st_pop(const KParams<C>& k, C v, int a, unsigned& r
 // population is d_a = dPsi * w_a, i.e. fbar_a = Psi rho_w w_a (Eq. nm.14).
 // Outgoing populations b (e_y < 0 at the bottom wall, e_y > 0 at the top)
 // cross the wall from their |e_y| rows nearest to it and are credited to the
-// column they land on, so the source column is x - e_x.  Accumulated in the
-// compute type (fp64 solves in fp64; fp32 and 16-bit storage in fp32, whose
-// ~1e-7 relative error matches the stored populations' own resolution).
+// column they land on, so the source column is x - e_x.  fp64 accumulation in
+// every precision; the fill d_a = dPsi w_a is formed in the compute type.
 template <typename S, typename C>
-__device__ __noinline__ C wall_dpsi(const KParams<C>& k, const S* __restrict__ src, int x,
+__device__ __noinline__ double wall_dpsi(const KParams<C>& k, const S* __restrict__ src, int x,
                                     bool bottom) {
-    C acc = C(0);
+    double acc = 0.0;
     for (int b = k.R; b < k.V; ++b) {
         const int ey = k.ey[b];
         if (bottom ? (ey >= 0) : (ey <= 0)) continue;
@@ -126,7 +125,7 @@ __device__ __noinline__ C wall_dpsi(const KParams<C>& k, const S* __restrict__ s
         const S* pl = src + (long long)b * k.plane + xs;
         for (int j = 0; j < n; ++j) {
             const int row = bottom ? j : (k.Ny - 1 - j);
-            acc += ld_pop<S, C>(k, pl[(long long)row * k.Nx], b);
+            acc += (double)ld_pop<S, C>(k, pl[(long long)row * k.Nx], b);
         }
     }
     return acc * k.inv_den;
@@ -439,8 +438,8 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
         if (!nb && !nt) {          // a node away from the walls in a tile that touches one
             pull_rows_any<SET, S, C>(k, k.srcf, cell, f);
         } else {
-        const C pb = nb ? wall_dpsi<S, C>(k, src, x, true) : C(0);
-        const C pt = nt ? wall_dpsi<S, C>(k, src, x, false) : C(0);
+        const C pb = nb ? C(wall_dpsi<S, C>(k, src, x, true)) : C(0);
+        const C pt = nt ? C(wall_dpsi<S, C>(k, src, x, false)) : C(0);
 #pragma unroll
         for (int a = 0; a < V; ++a) {
             const int ys = y - k.ey[a];
@@ -490,8 +489,8 @@ k_step_warp(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* 
         y = cell / k.Nx;
         x = cell - y * k.Nx;
     }
-    const C pb = (node && y < k.maxey) ? wall_dpsi<S, C>(k, src, x, true) : C(0);
-    const C pt = (node && y >= k.Ny - k.maxey) ? wall_dpsi<S, C>(k, src, x, false) : C(0);
+    const C pb = (node && y < k.maxey) ? C(wall_dpsi<S, C>(k, src, x, true)) : C(0);
+    const C pt = (node && y >= k.Ny - k.maxey) ? C(wall_dpsi<S, C>(k, src, x, false)) : C(0);
     auto value = [&](int a) -> C {
         const int ys = y - k.ey[a];
         if (ys < 0) return pb * k.cw[a];
@@ -564,8 +563,8 @@ k_generic(const __grid_constant__ KParams<C> k, const S* __restrict__ src,
     if (INIT) {
         r0 = rho0[cell] - 1.0;
     } else {
-        if (y < k.maxey) pb = wall_dpsi<S, C>(k, src, x, true);
-        if (y >= k.Ny - k.maxey) pt = wall_dpsi<S, C>(k, src, x, false);
+        if (y < k.maxey) pb = C(wall_dpsi<S, C>(k, src, x, true));
+        if (y >= k.Ny - k.maxey) pt = C(wall_dpsi<S, C>(k, src, x, false));
     }
     auto value = [&](int a) -> C {
         if (INIT) return C(r0 * k.w[a]);
