@@ -334,6 +334,7 @@ k_engine_resident(const EngineSolve<C>* __restrict__ solves, const ResBundle* __
     __shared__ ResChannel sch[kResMaxCh];
     __shared__ int wch[kResNodes / 32];     // channel of each run of 32 nodes, -1: padding
     __shared__ int s_b;
+    __shared__ int s_run[2];                 // per-step work counters
     const int nb = *nbundles_p;
     bundles += *bundle_off_p;
     const unsigned seed0 = *seed_p;
@@ -346,6 +347,7 @@ k_engine_resident(const EngineSolve<C>* __restrict__ solves, const ResBundle* __
         const ResBundle bd = bundles[bi];
         for (int c = threadIdx.x; c < bd.count; c += BT) sch[c] = chans[bd.first + c];
         for (int w = threadIdx.x; w < kResNodes / 32; w += BT) wch[w] = -1;
+        if (threadIdx.x == 0) s_run[0] = 0;
         __syncthreads();
         for (int c = threadIdx.x; c < bd.count; c += BT)
             for (int w = sch[c].start >> 5; w < (sch[c].start + sch[c].ncell + 31) >> 5; ++w) wch[w] = c;
@@ -371,23 +373,35 @@ k_engine_resident(const EngineSolve<C>* __restrict__ solves, const ResBundle* __
                 sb[plane_opp<SET>(a) * PS + (y + G) * Nx + x] = src[(long long)a * B.k.plane + cell];
         }
         __syncthreads();
+        // Each step, warps take runs of 32 nodes from a shared counter, so warps
+        // that drew wall nodes or a lighter share do not hold the others at the
+        // barrier.  Step i uses counter i & 1; the other one, last used in step
+        // i - 1 (finished at the barrier), is reset for step i + 1.
+        const int nruns = bd.nodes >> 5;
+        const int lane = threadIdx.x & 31;
 #pragma unroll 1
         for (int i = 0; i < K; ++i) {
             const unsigned seed = seed0 + unsigned(i & 1);
             const int emit = i == K - 1 ? 1 : (i == K - 2 ? 2 : 0);
+            if (threadIdx.x == 0) s_run[(i + 1) & 1] = 0;
 #pragma unroll 1
-            for (int j = 0; j < NPT; ++j) {
-                const int g = threadIdx.x + j * BT;
-                if (g >= bd.nodes) break;
-                const int c = wch[g >> 5];
+            for (;;) {
+                int run = 0;
+                if (lane == 0) run = atomicAdd(&s_run[i & 1], 1);
+                run = __shfl_sync(0xffffffffu, run, 0);
+                if (run >= nruns) break;
+                const int c = wch[run];
                 if (c < 0) continue;
                 const ResChannel ch = sch[c];
-                const int cell = g - ch.start;
-                if (cell >= ch.ncell) continue;
-                if (i & 1)
-                    res_node<SET, N, S, C, true>(solves[ch.slot], sm + ch.off, ch.slot, cell, seed, emit);
-                else
-                    res_node<SET, N, S, C, false>(solves[ch.slot], sm + ch.off, ch.slot, cell, seed, emit);
+                const int cell = run * 32 + lane - ch.start;
+                if (cell < ch.ncell) {
+                    if (i & 1)
+                        res_node<SET, N, S, C, true>(solves[ch.slot], sm + ch.off, ch.slot, cell,
+                                                     seed, emit);
+                    else
+                        res_node<SET, N, S, C, false>(solves[ch.slot], sm + ch.off, ch.slot, cell,
+                                                      seed, emit);
+                }
             }
             __syncthreads();
         }
