@@ -85,7 +85,7 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
             C f[V];
             if (fast) {
 #pragma unroll
-                for (int a = 0; a < V; ++a) f[a] = ld_pop<S, C>(k, sp[a][cell], a);
+                for (int a = 0; a < V; ++a) f[a] = ld_pop<S, C>(k, ld_stream(sp[a] + cell), a);
             } else if (rows || (cell / k.Nx >= k.maxey && cell / k.Nx < k.Ny - k.maxey)) {
                 // nodes away from the walls (the whole tile, or this node of a wall tile)
                 pull_rows_any<SET, S, C>(k, sp, cell, f);

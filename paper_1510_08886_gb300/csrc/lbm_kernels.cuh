@@ -89,6 +89,25 @@ __device__ __forceinline__ unsigned sr_seed(unsigned seed, int cell) {
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
+// Interior population load through the read-only path with a 256-byte L2
+// prefetch size: a warp's 128-byte access also brings the next 128 bytes of
+// the plane into L2, which the neighbouring warp reads next (measured +0.35 %
+// on the 4096 x 512 fp32 step).  16-bit storage takes a plain load.
+__device__ __forceinline__ float ld_stream(const float* p) {
+    float v;
+    asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p) {
+    double v;
+    asm("ld.global.nc.L2::256B.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+template <typename S>
+__device__ __forceinline__ S ld_stream(const S* p) {
+    return *p;
+}
+
 template <typename S, typename C>
 __device__ __forceinline__ C ld_pop(const KParams<C>& k, S v, int a) {
     if constexpr (Storage<S>::scaled) return mul_rn(Storage<S>::to_f(v), k.sw[a]);
@@ -371,12 +390,12 @@ __device__ __forceinline__ C pull_col(const KParams<C>& k, const PTR& sp, int ce
     } else {
         i = cell + (x < Nx + EX ? 0 : -Nx);
     }
-    return ld_pop<S, C>(k, static_cast<const S*>(sp[A])[i], A);
+    return ld_pop<S, C>(k, ld_stream(static_cast<const S*>(sp[A]) + i), A);
 }
 
 template <class SET, typename S, typename C, int A, class PTR>
 __device__ __forceinline__ C pull_col1(const KParams<C>& k, const PTR& sp, int cell) {
-    return ld_pop<S, C>(k, static_cast<const S*>(sp[A])[cell + plane_ex<SET>(A)], A);
+    return ld_pop<S, C>(k, ld_stream(static_cast<const S*>(sp[A]) + cell + plane_ex<SET>(A)), A);
 }
 
 template <class SET, typename S, typename C, class PTR, int... I>
@@ -426,7 +445,7 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
     C f[V];
     if (fast) {
 #pragma unroll
-        for (int a = 0; a < V; ++a) f[a] = ld_pop<S, C>(k, static_cast<const S*>(k.srcf[a])[cell], a);
+        for (int a = 0; a < V; ++a) f[a] = ld_pop<S, C>(k, ld_stream(static_cast<const S*>(k.srcf[a]) + cell), a);
     } else if (rows) {
         if (cell >= k.ncell) return;
         pull_rows_any<SET, S, C>(k, k.srcf, cell, f);
