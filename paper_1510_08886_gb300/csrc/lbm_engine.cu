@@ -39,6 +39,7 @@ namespace {
 
 constexpr int kGroups = 18;        // 6 compiled velocity sets x Hermite orders 2..4
 constexpr int kMaxChunk = 1000;    // steps per captured chunk
+constexpr int kLanes = 4;          // concurrent streams inside a captured chunk
 
 size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
 
@@ -165,8 +166,8 @@ struct lbm_engine {
     lbm::ResChannel* d_chans = nullptr;        // max_slots entries
     int* d_nbundles = nullptr;                 // per group: counts, then offsets
     int* d_rcounters = nullptr;                // per group
-    cudaStream_t side = nullptr;               // fork of the chunk graph
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side[kLanes - 1] = {};        // forks of the chunk graph
+    cudaEvent_t ev_fork = nullptr, ev_join[kLanes - 1] = {};
     std::vector<GroupWork> plan;               // present groups and their work
     cudaGraphExec_t exec = nullptr;
 };
@@ -354,52 +355,60 @@ int rebuild_tiles(lbm_engine* e) {
 }
 
 // One chunk of K steps + the reductions + the seed advance, on the stream.
-// Resident bundles (K steps per launch) run on a fork of the stream beside
-// the per-step tiled launches; both touch disjoint solves.
+// Independent work items run on forks of the stream inside the captured
+// chunk: the resident bundles of all groups (K steps per launch) and the K
+// per-step launches of each group's tiles.  The items touch disjoint solves,
+// so they overlap on the GPU and one group's kernel tail is filled by
+// another's blocks.  Items are dealt to kLanes streams in order.
 int enqueue_chunk(lbm_engine* e) {
     bool any_t = false, any_r = false;
+    int items = 0;
     for (const GroupWork& w : e->plan) {
         any_t |= w.tiled;
         any_r |= w.res;
+        items += w.tiled;
     }
+    items += any_r;
     cudaError_t err = cudaSuccess;
     if (any_t) err = cudaMemsetAsync(e->d_counters, 0, sizeof(int) * kGroups * e->K, e->stream);
     if (any_r && err == cudaSuccess)
         err = cudaMemsetAsync(e->d_rcounters, 0, sizeof(int) * kGroups, e->stream);
     if (err != cudaSuccess) return cuda_rc(err);
-    const bool fork = any_t && any_r;
-    cudaStream_t rs = fork ? e->side : e->stream;
-    if (fork) {
+    const int lanes = std::min(items, kLanes);
+    auto lane = [&](int item) { return item % kLanes == 0 ? e->stream : e->side[item % kLanes - 1]; };
+    if (lanes > 1) {
         err = cudaEventRecord(e->ev_fork, e->stream);
-        if (err == cudaSuccess) err = cudaStreamWaitEvent(e->side, e->ev_fork, 0);
+        for (int l = 1; l < lanes && err == cudaSuccess; ++l)
+            err = cudaStreamWaitEvent(e->side[l - 1], e->ev_fork, 0);
         if (err != cudaSuccess) return cuda_rc(err);
+    }
+    int item = 0;
+    if (any_r) {
+        const cudaStream_t rs = lane(item++);
+        for (const GroupWork& w : e->plan) {
+            if (!w.res) continue;
+            lbm::ResidentLaunch L{};
+            L.solves = e->d_solves;
+            L.bundles = e->d_bundles;
+            L.chans = e->d_chans;
+            L.nbundles = e->d_nbundles + w.g;
+            L.bundle_off = e->d_nbundles + kGroups + w.g;
+            L.counter = e->d_rcounters + w.g;
+            L.seed = e->d_seed;
+            L.K = e->K;
+            L.grid = w.rgrid;
+            L.smem = e->res_smem;
+            const int set = w.g / 3, N = w.g % 3 + 2;
+            err = e->precision == LBM_FP16   ? lbm::engine_resident_half(set, N, L, rs)
+                  : e->precision == LBM_BF16 ? lbm::engine_resident_bf16(set, N, L, rs)
+                                             : lbm::engine_resident_fp32(set, N, L, rs);
+            if (err != cudaSuccess) return cuda_rc(err);
+        }
     }
     for (const GroupWork& w : e->plan) {
-        if (!w.res) continue;
-        lbm::ResidentLaunch L{};
-        L.solves = e->d_solves;
-        L.bundles = e->d_bundles;
-        L.chans = e->d_chans;
-        L.nbundles = e->d_nbundles + w.g;
-        L.bundle_off = e->d_nbundles + kGroups + w.g;
-        L.counter = e->d_rcounters + w.g;
-        L.seed = e->d_seed;
-        L.K = e->K;
-        L.grid = w.rgrid;
-        L.smem = e->res_smem;
-        const int set = w.g / 3, N = w.g % 3 + 2;
-        err = e->precision == LBM_FP16   ? lbm::engine_resident_half(set, N, L, rs)
-              : e->precision == LBM_BF16 ? lbm::engine_resident_bf16(set, N, L, rs)
-                                         : lbm::engine_resident_fp32(set, N, L, rs);
-        if (err != cudaSuccess) return cuda_rc(err);
-    }
-    if (fork) {
-        err = cudaEventRecord(e->ev_join, e->side);
-        if (err != cudaSuccess) return cuda_rc(err);
-    }
-    for (int i = 0; i < e->K && any_t; ++i) {
-        for (const GroupWork& w : e->plan) {
-            if (!w.tiled) continue;
+        if (!w.tiled) continue;
+        const cudaStream_t ts = lane(item++);
+        for (int i = 0; i < e->K; ++i) {
             lbm::EngineLaunch L{};
             L.solves = e->d_solves;
             L.tiles = e->d_tiles;
@@ -412,14 +421,15 @@ int enqueue_chunk(lbm_engine* e) {
             L.chunk = e->grab;
             L.grid = w.grid;
             const int set = w.g / 3, N = w.g % 3 + 2;
-            err = e->precision == LBM_FP16   ? lbm::engine_step_half(set, N, L, e->stream)
-                  : e->precision == LBM_BF16 ? lbm::engine_step_bf16(set, N, L, e->stream)
-                                             : lbm::engine_step_fp32(set, N, L, e->stream);
+            err = e->precision == LBM_FP16   ? lbm::engine_step_half(set, N, L, ts)
+                  : e->precision == LBM_BF16 ? lbm::engine_step_bf16(set, N, L, ts)
+                                             : lbm::engine_step_fp32(set, N, L, ts);
             if (err != cudaSuccess) return cuda_rc(err);
         }
     }
-    if (fork) {
-        err = cudaStreamWaitEvent(e->stream, e->ev_join, 0);
+    for (int l = 1; l < lanes; ++l) {
+        err = cudaEventRecord(e->ev_join[l - 1], e->side[l - 1]);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(e->stream, e->ev_join[l - 1], 0);
         if (err != cudaSuccess) return cuda_rc(err);
     }
     err = lbm::engine_reduce(e->d_solves, e->d_active, e->d_results, e->max_slots, e->stream);
@@ -548,9 +558,11 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
         err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     // the resident kernels' static shared memory is under 2 KiB
     e->res_smem = optin > 4096 ? size_t(optin - 4096) & ~size_t(255) : 0;
-    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->side, cudaStreamNonBlocking);
+    for (int l = 0; l < kLanes - 1 && err == cudaSuccess; ++l) {
+        err = cudaStreamCreateWithFlags(&e->side[l], cudaStreamNonBlocking);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->ev_join[l], cudaEventDisableTiming);
+    }
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming);
-    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->ev_join, cudaEventDisableTiming);
     if (err == cudaSuccess) {
         if (stream) {
             e->stream = static_cast<cudaStream_t>(stream);
@@ -574,8 +586,10 @@ void lbm_engine_destroy(lbm_engine* e) {
     if (e->stream) cudaStreamSynchronize(e->stream);
     if (e->exec) cudaGraphExecDestroy(e->exec);
     if (e->ev_fork) cudaEventDestroy(e->ev_fork);
-    if (e->ev_join) cudaEventDestroy(e->ev_join);
-    if (e->side) cudaStreamDestroy(e->side);
+    for (int l = 0; l < kLanes - 1; ++l) {
+        if (e->ev_join[l]) cudaEventDestroy(e->ev_join[l]);
+        if (e->side[l]) cudaStreamDestroy(e->side[l]);
+    }
     if (e->own_arena && e->base) cudaFree(e->base);
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
     delete e;
