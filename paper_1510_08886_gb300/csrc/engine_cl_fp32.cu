@@ -1,0 +1,14 @@
+// Cluster-split resident engine kernels, fp32 population storage.
+#include "engine_launch.cuh"
+
+namespace lbm {
+
+cudaError_t engine_cluster_fp32(int set_id, int N, const ClusterLaunch& L, cudaStream_t st) {
+    return engine_cluster_t<float>(set_id, N, L, st);
+}
+
+int engine_cluster_attr_fp32(int set_id, int N, size_t smem) {
+    return engine_cluster_attr_t<float>(set_id, N, smem);
+}
+
+}  // namespace lbm

@@ -9,6 +9,8 @@
 // relaxation), with the solve's constants read from its device record.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "lbm_kernels.cuh"
 
 namespace lbm {
@@ -252,14 +254,43 @@ __device__ __forceinline__ void res_push(const KParams<C>& k, S* sb, int PS, int
     }
 }
 
-// One node of one A or B step.
+// Moments, equilibrium, force and relaxation of one node (f in place): the
+// arithmetic of k_engine_step.
+template <class SET, int N, typename C>
+__device__ __forceinline__ CellCoef<C> res_collide(const KParams<C>& k, C* f) {
+    constexpr int R = SET::R, P = SET::P;
+    C drho = R ? f[0] : C(0), Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
+    moments_ct<SET, C>(f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, P>{});
+    const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, Kxy, Kyy);
+    if (R) f[0] = fma(k.one_m_omega, f[0], k.omw_rest * q.a0);
+    if (k.force)
+        relax_ct<SET, N, true, C>(k, q, f, std::make_integer_sequence<int, P>{});
+    else
+        relax_ct<SET, N, false, C>(k, q, f, std::make_integer_sequence<int, P>{});
+    return q;
+}
+
+template <typename C>
+__device__ __forceinline__ void res_emit(const EngineSolve<C>& B, const CellCoef<C>& q, int cell,
+                                         int emit) {
+    if (emit == 1) {
+        B.rho[cell] = 1.0 + (double)q.drho;
+        B.ux[cell] = (double)q.ux;
+        B.uy[cell] = (double)q.uy;
+    } else if (emit == 2) {
+        B.prev[cell] = (double)q.ux;
+    }
+    flag_density<C>(q, B.status);
+}
+
+// One node of one A or B step.  sb: the channel's planes (PS elements each,
+// row y of the channel at row y + G of a plane).
 template <class SET, int N, typename S, typename C, bool STEP_A>
-__device__ __forceinline__ void res_node(const EngineSolve<C>& B, S* sb, int slot, int cell,
+__device__ __forceinline__ void res_node(const EngineSolve<C>& B, S* sb, int PS, int slot, int cell,
                                          unsigned seed, int emit) {
     constexpr int R = SET::R, P = SET::P, V = R + 2 * P, G = set_maxey<SET>();
     const KParams<C>& k = B.k;
     const int Nx = k.Nx, Ny = k.Ny;
-    const int PS = Nx * (Ny + 2 * G);
     const int y = Nx == 1 ? cell : cell / Nx;     // one-column channels need no division
     const int x = cell - y * Nx;
     C f[V];
@@ -292,14 +323,7 @@ __device__ __forceinline__ void res_node(const EngineSolve<C>& B, S* sb, int slo
             }
         }
     }
-    C drho = R ? f[0] : C(0), Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
-    moments_ct<SET, C>(f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, P>{});
-    const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, Kxy, Kyy);
-    if (R) f[0] = fma(k.one_m_omega, f[0], k.omw_rest * q.a0);
-    if (k.force)
-        relax_ct<SET, N, true, C>(k, q, f, std::make_integer_sequence<int, P>{});
-    else
-        relax_ct<SET, N, false, C>(k, q, f, std::make_integer_sequence<int, P>{});
+    const CellCoef<C> q = res_collide<SET, N, C>(k, f);
     const unsigned rs = sr_seed<S, C>(seed + unsigned(slot) * 0x632be5abu, cell);
     if (mode == 0)
         res_push<SET, S, C, 0, STEP_A>(k, sb, PS, x, y, f, rs, std::make_integer_sequence<int, V>{});
@@ -307,14 +331,7 @@ __device__ __forceinline__ void res_node(const EngineSolve<C>& B, S* sb, int slo
         res_push<SET, S, C, 1, STEP_A>(k, sb, PS, x, y, f, rs, std::make_integer_sequence<int, V>{});
     else
         res_push<SET, S, C, 2, STEP_A>(k, sb, PS, x, y, f, rs, std::make_integer_sequence<int, V>{});
-    if (emit == 1) {
-        B.rho[cell] = 1.0 + (double)q.drho;
-        B.ux[cell] = (double)q.ux;
-        B.uy[cell] = (double)q.uy;
-    } else if (emit == 2) {
-        B.prev[cell] = (double)q.ux;
-    }
-    flag_density<C>(q, B.status);
+    res_emit<C>(B, q, cell, emit);
 }
 
 // Persistent blocks (one per SM) take bundles from an atomic counter; each
@@ -395,12 +412,12 @@ k_engine_resident(const EngineSolve<C>* __restrict__ solves, const ResBundle* __
                 const ResChannel ch = sch[c];
                 const int cell = run * 32 + lane - ch.start;
                 if (cell < ch.ncell) {
+                    const EngineSolve<C>& B = solves[ch.slot];
+                    const int PS = B.k.Nx * (B.k.Ny + 2 * G);
                     if (i & 1)
-                        res_node<SET, N, S, C, true>(solves[ch.slot], sm + ch.off, ch.slot, cell,
-                                                     seed, emit);
+                        res_node<SET, N, S, C, true>(B, sm + ch.off, PS, ch.slot, cell, seed, emit);
                     else
-                        res_node<SET, N, S, C, false>(solves[ch.slot], sm + ch.off, ch.slot, cell,
-                                                      seed, emit);
+                        res_node<SET, N, S, C, false>(B, sm + ch.off, PS, ch.slot, cell, seed, emit);
                 }
             }
             __syncthreads();
@@ -424,6 +441,145 @@ k_engine_resident(const EngineSolve<C>* __restrict__ solves, const ResBundle* __
             for (int a = 0; a < V; ++a)
                 dst[(long long)a * B.k.plane + cell] = sb[plane_opp<SET>(a) * PS + (y + G) * Nx + x];
         }
+    }
+}
+
+// ---- resident chunks split over a thread-block cluster ----------------------
+// A one-column channel (Nx = 1) advanced by a cluster of kClusterCTAs blocks on
+// as many SMs: block q owns rows [q Rs, (q + 1) Rs), Rs = ceil(Ny / kClusterCTAs),
+// stored at rows G.. of its own planes (LP = Rs + 2 G elements each); the
+// wall ghost rows belong to the first and the last block.  Nodes whose
+// accesses stay in their own block (at least G rows from an inner slab
+// boundary) take res_node on the block's planes; the others reach the
+// neighbouring block's shared memory through the cluster (distributed shared
+// memory).  The same two-step in-place streaming, fills, sums and collision
+// as the single-block resident kernel, one cluster barrier per step: the
+// results are bitwise those of the other paths.  A channel runs its chunk on
+// kClusterCTAs SMs instead of one, which shortens its time to steady state
+// when the GPU has SMs to spare.
+
+constexpr int kClusterCTAs = 4;
+constexpr int kClusterThreads = 512;
+
+// Element (plane, global row) of the channel in the shared memory of the
+// block that owns the row (the calling block's own row: a local address).
+template <typename S>
+__device__ __forceinline__ S* cl_at(cooperative_groups::cluster_group& cl, S* sm, int LP, int Rs,
+                                    int Ny, int G, int plane, int row) {
+    const int own = row < 0 ? 0 : (row >= Ny ? kClusterCTAs - 1 : row / Rs);
+    return cl.map_shared_rank(sm + plane * LP + (row - own * Rs + G), own);
+}
+
+// One node near an inner slab boundary (Nx = 1): the general path of
+// res_node with every shared-memory access through cl_at.
+template <class SET, int N, typename S, typename C, bool STEP_A>
+__device__ __noinline__ void res_node_cluster(const EngineSolve<C>& B, S* sm, int LP, int Rs,
+                                              int slot, int y, unsigned seed, int emit) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    constexpr int R = SET::R, P = SET::P, V = R + 2 * P, G = set_maxey<SET>();
+    const KParams<C>& k = B.k;
+    const int Ny = k.Ny;
+    auto wall = [&](bool bottom) {
+        double acc = 0.0;
+        for (int b = k.R; b < k.V; ++b) {
+            const int ey = k.ey[b];
+            if (bottom ? (ey >= 0) : (ey <= 0)) continue;
+            const int n = bottom ? -ey : ey;
+            const int bb = b < k.R + k.P ? b + k.P : b - k.P;
+            for (int j = 0; j < n; ++j) {
+                const int row = bottom ? j : (Ny - 1 - j);
+                const S v = STEP_A ? *cl_at(cl, sm, LP, Rs, Ny, G, b, row + ey)
+                                   : *cl_at(cl, sm, LP, Rs, Ny, G, bb, row);
+                acc += (double)ld_pop<S, C>(k, v, b);
+            }
+        }
+        return acc * k.inv_den;
+    };
+    const C pb = y < G ? C(wall(true)) : C(0);
+    const C pt = y >= Ny - G ? C(wall(false)) : C(0);
+    C f[V];
+#pragma unroll
+    for (int a = 0; a < V; ++a) {
+        const int ys = y - k.ey[a];
+        if (ys < 0) {
+            f[a] = pb * k.cw[a];
+        } else if (ys >= Ny) {
+            f[a] = pt * k.cw[a];
+        } else if (STEP_A) {
+            f[a] = ld_pop<S, C>(k, *cl_at(cl, sm, LP, Rs, Ny, G, a, y), a);
+        } else {
+            const int ab = a < R ? a : (a < R + P ? a + P : a - P);
+            f[a] = ld_pop<S, C>(k, *cl_at(cl, sm, LP, Rs, Ny, G, ab, ys), a);
+        }
+    }
+    const CellCoef<C> q = res_collide<SET, N, C>(k, f);
+    unsigned rs = sr_seed<S, C>(seed + unsigned(slot) * 0x632be5abu, y);
+#pragma unroll
+    for (int a = 0; a < V; ++a) {
+        const S v = st_pop<S, C>(k, f[a], a, rs);
+        if (STEP_A)
+            *cl_at(cl, sm, LP, Rs, Ny, G, plane_opp<SET>(a), y) = v;
+        else
+            *cl_at(cl, sm, LP, Rs, Ny, G, a, y + k.ey[a]) = v;
+    }
+    res_emit<C>(B, q, y, emit);
+}
+
+// Cluster c (blocks c * kClusterCTAs ..) advances channel slots[c] by K (even)
+// steps; clusters beyond *count_p exit at once, all their blocks together.
+template <class SET, int N, typename S, typename C>
+__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kClusterThreads, 1)
+k_engine_cluster(const EngineSolve<C>* __restrict__ solves, const int* __restrict__ slots,
+                 const int* __restrict__ count_p, const int* __restrict__ off_p,
+                 const unsigned* __restrict__ seed_p, int K) {
+    namespace cg = cooperative_groups;
+    constexpr int V = SET::R + 2 * SET::P, G = set_maxey<SET>();
+    extern __shared__ __align__(16) unsigned char cl_smem[];
+    S* const sm = reinterpret_cast<S*>(cl_smem);
+    cg::cluster_group cl = cg::this_cluster();
+    const int cid = blockIdx.x / kClusterCTAs;
+    if (cid >= *count_p) return;                      // uniform over the cluster
+    const int q = int(cl.block_rank());
+    const int slot = slots[*off_p + cid];
+    const EngineSolve<C>& B = solves[slot];
+    const int Ny = B.k.Ny;
+    const int Rs = (Ny + kClusterCTAs - 1) / kClusterCTAs;
+    const int LP = Rs + 2 * G;
+    const int y0 = q * Rs, y1 = min(y0 + Rs, Ny);
+    S* const sloc = sm - y0;                          // global row y at local row y - y0 (+ G)
+    const long long plane = B.k.plane;
+    // load the own rows into the opposite planes, as an A step leaves them
+    {
+        const S* src = static_cast<const S*>(B.f[B.phase]);
+        for (int y = y0 + threadIdx.x; y < y1; y += kClusterThreads)
+#pragma unroll
+            for (int a = 0; a < V; ++a) sloc[plane_opp<SET>(a) * LP + y + G] = src[a * plane + y];
+    }
+    cl.sync();                                        // every block started and loaded
+    const unsigned seed0 = *seed_p;
+#pragma unroll 1
+    for (int i = 0; i < K; ++i) {
+        const unsigned seed = seed0 + unsigned(i & 1);
+        const int emit = i == K - 1 ? 1 : (i == K - 2 ? 2 : 0);
+#pragma unroll 1
+        for (int y = y0 + threadIdx.x; y < y1; y += kClusterThreads) {
+            const bool local = (q == 0 || y - G >= y0) && (q == kClusterCTAs - 1 || y + G < y0 + Rs);
+            if (i & 1) {
+                if (local) res_node<SET, N, S, C, true>(B, sloc, LP, slot, y, seed, emit);
+                else res_node_cluster<SET, N, S, C, true>(B, sm, LP, Rs, slot, y, seed, emit);
+            } else {
+                if (local) res_node<SET, N, S, C, false>(B, sloc, LP, slot, y, seed, emit);
+                else res_node_cluster<SET, N, S, C, false>(B, sm, LP, Rs, slot, y, seed, emit);
+            }
+        }
+        cl.sync();
+    }
+    {
+        S* dst = static_cast<S*>(B.f[B.phase]);
+        for (int y = y0 + threadIdx.x; y < y1; y += kClusterThreads)
+#pragma unroll
+            for (int a = 0; a < V; ++a) dst[a * plane + y] = sloc[plane_opp<SET>(a) * LP + y + G];
     }
 }
 
