@@ -290,20 +290,10 @@ int lbm_engine_set_chunk(lbm_engine* e, int steps);
  * lbm_engine_autotune.  LBM_EINVAL unless enable is 0 or 1. */
 int lbm_engine_set_resident(lbm_engine* e, int enable);
 
-/* Resident chunks on thread-block clusters on (1, the default) or off (0).
- * When a velocity set has at most (SMs / 4) resident solves, its one-column
- * solves (Nx = 1) with Ny >= 256 each run their chunk on a cluster of 4
- * blocks on 4 SMs, each block holding a quarter of the rows and reaching its
- * neighbours' rows through the cluster's shared memory, instead of on one
- * SM: a lightly loaded engine finishes each such solve sooner.  Results are
- * bitwise those of the other paths.  Takes effect at the next lbm_engine_run
- * or lbm_engine_autotune.  LBM_EINVAL unless enable is 0 or 1. */
-int lbm_engine_set_cluster(lbm_engine* e, int enable);
-
-/* How many solves take each path at the next chunk: per-step tiles, resident
- * bundles (one block), resident clusters.  Any pointer may be NULL.  Applies
+/* How many solves take each path at the next chunk: per-step tiles and
+ * resident (shared-memory) bundles.  Either pointer may be NULL.  Applies
  * pending admissions and removals (as lbm_engine_run would). */
-int lbm_engine_paths(lbm_engine* e, int* tiled, int* bundled, int* clustered);
+int lbm_engine_paths(lbm_engine* e, int* tiled, int* resident);
 
 /* Advance every resident solve by chunks * K steps, then copy the per-slot
  * results to `results` (host, 4 * max_solves doubles, may be NULL):

@@ -325,13 +325,11 @@ class Engine:
     ``chunk`` steps (one CUDA-graph replay per chunk) and released with
     ``remove``.  The arena is a torch uint8 tensor on the current device.
     ``resident`` runs solves that fit in shared memory a whole chunk per
-    launch (bitwise the same results as the per-step launches); ``cluster``
-    lets a lightly loaded engine run tall one-column solves on clusters of 4
-    SMs (bitwise the same results again).
+    launch (bitwise the same results as the per-step launches).
     """
 
     def __init__(self, precision="fp32", max_solves=256, arena_bytes=1 << 30, stream=None,
-                 chunk=100, resident=True, cluster=True):
+                 chunk=100, resident=True):
         torch = _torch_cuda()
         self._torch = torch
         self.precision = precision
@@ -349,7 +347,6 @@ class Engine:
         self.results = np.zeros((self.max_solves, 4))
         self.set_chunk(chunk)
         self.set_resident(resident)
-        self.set_cluster(cluster)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -379,16 +376,12 @@ class Engine:
               "lbm_engine_set_resident")
         self.resident = bool(enable)
 
-    def set_cluster(self, enable):
-        check(_lib.lib().lbm_engine_set_cluster(self._h, int(bool(enable))), "lbm_engine_set_cluster")
-        self.cluster = bool(enable)
-
     def paths(self):
-        """Solves per path at the next chunk: (tiled, bundled, clustered)."""
-        t, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
-        check(_lib.lib().lbm_engine_paths(self._h, ctypes.byref(t), ctypes.byref(b),
-                                          ctypes.byref(c)), "lbm_engine_paths")
-        return t.value, b.value, c.value
+        """Solves per path at the next chunk: (tiled, resident)."""
+        t, r = ctypes.c_int(0), ctypes.c_int(0)
+        check(_lib.lib().lbm_engine_paths(self._h, ctypes.byref(t), ctypes.byref(r)),
+              "lbm_engine_paths")
+        return t.value, r.value
 
     def add(self, e, w, c, order, Nx, Ny, Kn, force, rho=None):
         d = _DVM(e, w, c)

@@ -77,8 +77,7 @@ SIGNATURES = {
     "lbm_engine_remove": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_engine_set_chunk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_engine_set_resident": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
-    "lbm_engine_set_cluster": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
-    "lbm_engine_paths": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p, c_int_p]),
+    "lbm_engine_paths": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p]),
     "lbm_engine_state_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_size_t)]),
     "lbm_engine_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,

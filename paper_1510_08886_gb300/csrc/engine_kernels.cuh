@@ -9,8 +9,6 @@
 // relaxation), with the solve's constants read from its device record.
 #pragma once
 
-#include <cooperative_groups.h>
-
 #include "lbm_kernels.cuh"
 
 namespace lbm {
@@ -94,19 +92,7 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
             } else {
                 const int y = cell / k.Nx;
                 const int x = cell - y * k.Nx;
-                const bool nb = y < k.maxey, nt = y >= k.Ny - k.maxey;
-                const C pb = nb ? C(wall_dpsi<S, C>(k, src, x, true)) : C(0);
-                const C pt = nt ? C(wall_dpsi<S, C>(k, src, x, false)) : C(0);
-#pragma unroll
-                for (int a = 0; a < V; ++a) {
-                    const int ys = y - k.ey[a];
-                    if (ys < 0)
-                        f[a] = pb * k.cw[a];
-                    else if (ys >= k.Ny)
-                        f[a] = pt * k.cw[a];
-                    else
-                        f[a] = pull<S, C>(k, src, a, x, y);
-                }
+                pull_wall_ct<SET, S, C>(k, src, x, y, f, std::make_integer_sequence<int, V>{});
             }
             C drho = R ? f[0] : C(0), Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
             moments_ct<SET, C>(f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, P>{});
@@ -201,29 +187,52 @@ __device__ __forceinline__ int xwrap(int x, int Nx) {
 }
 
 // Flux balance of Eq. nm.15 for landing column x from shared memory: the
-// same sum, in the same order, as wall_dpsi.  In a B step the leaving
+// same terms, in the same order, as wall_dpsi.  In a B step the leaving
 // population b of node m = (x - e_x, j) sits at (m, bbar); in an A step it
 // sits in the ghost row at (m + e_b, b).
-template <typename S, typename C>
-__device__ __noinline__ double res_wall_dpsi(const KParams<C>& k, const S* sb, int PS, int G, int x,
-                                        bool bottom, bool stepA) {
+template <class SET, typename S, typename C, bool BOTTOM, bool STEP_A>
+__device__ __forceinline__ double res_wall_dpsi(const KParams<C>& k, const S* sb, int PS, int x) {
+    constexpr int V = SET::R + 2 * SET::P, G = set_maxey<SET>();
     const int Nx = k.Nx;
-    double acc = 0.0;
-    for (int b = k.R; b < k.V; ++b) {
-        const int ey = k.ey[b];
-        if (bottom ? (ey >= 0) : (ey <= 0)) continue;
-        const int n = bottom ? -ey : ey;
-        const int bb = b < k.R + k.P ? b + k.P : b - k.P;
-        int xs = x - k.sx[b];
-        xs += (xs < 0) ? Nx : 0;
-        for (int j = 0; j < n; ++j) {
-            const int row = bottom ? j : (k.Ny - 1 - j);
-            const S v = stepA ? sb[(long long)b * PS + (long long)(row + ey + G) * Nx + x]
-                              : sb[(long long)bb * PS + (long long)(row + G) * Nx + xs];
-            acc += (double)ld_pop<S, C>(k, v, b);
+    auto term = [&](auto bc, int j) {
+        constexpr int b = decltype(bc)::value;
+        const int row = BOTTOM ? j : (k.Ny - 1 - j);
+        S v;
+        if (STEP_A) {
+            v = sb[b * PS + (row + plane_ey<SET>(b) + G) * Nx + x];
+        } else {
+            int xs = x - k.sx[b];
+            xs += (xs < 0) ? Nx : 0;
+            v = sb[plane_opp<SET>(b) * PS + (row + G) * Nx + xs];
         }
-    }
-    return acc * k.inv_den;
+        return (double)ld_pop<S, C>(k, v, b);
+    };
+    return wall_sum_ct<SET, BOTTOM>(term, std::make_integer_sequence<int, V>{}) * k.inv_den;
+}
+
+// Population A of a wall node from shared memory (fill or in-domain value).
+template <class SET, typename S, typename C, bool STEP_A, int A>
+__device__ __forceinline__ C res_wall_value(const KParams<C>& k, const S* sb, int PS, int x, int y,
+                                            C pb, C pt) {
+    constexpr int G = set_maxey<SET>();
+    constexpr int EY = plane_ey<SET>(A);
+    const int Nx = k.Nx;
+    const int ys = y - EY;
+    if (ys < 0) return pb * k.cw[A];
+    if (ys >= k.Ny) return pt * k.cw[A];
+    if (STEP_A) return ld_pop<S, C>(k, sb[A * PS + (y + G) * Nx + x], A);
+    int xs = x - k.sx[A];
+    xs += (xs < 0) ? Nx : 0;
+    return ld_pop<S, C>(k, sb[plane_opp<SET>(A) * PS + (ys + G) * Nx + xs], A);
+}
+
+template <class SET, typename S, typename C, bool STEP_A, int... I>
+__device__ __forceinline__ void res_pull_wall(const KParams<C>& k, const S* sb, int PS, int x, int y,
+                                              C* f, std::integer_sequence<int, I...>) {
+    constexpr int G = set_maxey<SET>();
+    const C pb = y < G ? C(res_wall_dpsi<SET, S, C, true, STEP_A>(k, sb, PS, x)) : C(0);
+    const C pt = y >= k.Ny - G ? C(res_wall_dpsi<SET, S, C, false, STEP_A>(k, sb, PS, x)) : C(0);
+    ((f[I] = res_wall_value<SET, S, C, STEP_A, I>(k, sb, PS, x, y, pb, pt)), ...);
 }
 
 template <class SET, typename S, typename C, int MODE, bool STEP_A, int... I>
@@ -303,25 +312,7 @@ __device__ __forceinline__ void res_node(const EngineSolve<C>& B, S* sb, int PS,
         else
             res_pull<SET, S, C, 2, STEP_A>(k, sb, PS, x, y, f, std::make_integer_sequence<int, V>{});
     } else {
-        const bool nb = y < G, nt = y >= Ny - G;
-        const C pb = nb ? C(res_wall_dpsi<S, C>(k, sb, PS, G, x, true, STEP_A)) : C(0);
-        const C pt = nt ? C(res_wall_dpsi<S, C>(k, sb, PS, G, x, false, STEP_A)) : C(0);
-#pragma unroll
-        for (int a = 0; a < V; ++a) {
-            const int ys = y - k.ey[a];
-            if (ys < 0) {
-                f[a] = pb * k.cw[a];
-            } else if (ys >= Ny) {
-                f[a] = pt * k.cw[a];
-            } else if (STEP_A) {
-                f[a] = ld_pop<S, C>(k, sb[(long long)a * PS + (long long)(y + G) * Nx + x], a);
-            } else {
-                int xs = x - k.sx[a];
-                xs += (xs < 0) ? Nx : 0;
-                const int ab = a < R ? a : (a < R + P ? a + P : a - P);
-                f[a] = ld_pop<S, C>(k, sb[(long long)ab * PS + (long long)(ys + G) * Nx + xs], a);
-            }
-        }
+        res_pull_wall<SET, S, C, STEP_A>(k, sb, PS, x, y, f, std::make_integer_sequence<int, V>{});
     }
     const CellCoef<C> q = res_collide<SET, N, C>(k, f);
     const unsigned rs = sr_seed<S, C>(seed + unsigned(slot) * 0x632be5abu, cell);
@@ -441,145 +432,6 @@ k_engine_resident(const EngineSolve<C>* __restrict__ solves, const ResBundle* __
             for (int a = 0; a < V; ++a)
                 dst[(long long)a * B.k.plane + cell] = sb[plane_opp<SET>(a) * PS + (y + G) * Nx + x];
         }
-    }
-}
-
-// ---- resident chunks split over a thread-block cluster ----------------------
-// A one-column channel (Nx = 1) advanced by a cluster of kClusterCTAs blocks on
-// as many SMs: block q owns rows [q Rs, (q + 1) Rs), Rs = ceil(Ny / kClusterCTAs),
-// stored at rows G.. of its own planes (LP = Rs + 2 G elements each); the
-// wall ghost rows belong to the first and the last block.  Nodes whose
-// accesses stay in their own block (at least G rows from an inner slab
-// boundary) take res_node on the block's planes; the others reach the
-// neighbouring block's shared memory through the cluster (distributed shared
-// memory).  The same two-step in-place streaming, fills, sums and collision
-// as the single-block resident kernel, one cluster barrier per step: the
-// results are bitwise those of the other paths.  A channel runs its chunk on
-// kClusterCTAs SMs instead of one, which shortens its time to steady state
-// when the GPU has SMs to spare.
-
-constexpr int kClusterCTAs = 4;
-constexpr int kClusterThreads = 512;
-
-// Element (plane, global row) of the channel in the shared memory of the
-// block that owns the row (the calling block's own row: a local address).
-template <typename S>
-__device__ __forceinline__ S* cl_at(cooperative_groups::cluster_group& cl, S* sm, int LP, int Rs,
-                                    int Ny, int G, int plane, int row) {
-    const int own = row < 0 ? 0 : (row >= Ny ? kClusterCTAs - 1 : row / Rs);
-    return cl.map_shared_rank(sm + plane * LP + (row - own * Rs + G), own);
-}
-
-// One node near an inner slab boundary (Nx = 1): the general path of
-// res_node with every shared-memory access through cl_at.
-template <class SET, int N, typename S, typename C, bool STEP_A>
-__device__ __noinline__ void res_node_cluster(const EngineSolve<C>& B, S* sm, int LP, int Rs,
-                                              int slot, int y, unsigned seed, int emit) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    constexpr int R = SET::R, P = SET::P, V = R + 2 * P, G = set_maxey<SET>();
-    const KParams<C>& k = B.k;
-    const int Ny = k.Ny;
-    auto wall = [&](bool bottom) {
-        double acc = 0.0;
-        for (int b = k.R; b < k.V; ++b) {
-            const int ey = k.ey[b];
-            if (bottom ? (ey >= 0) : (ey <= 0)) continue;
-            const int n = bottom ? -ey : ey;
-            const int bb = b < k.R + k.P ? b + k.P : b - k.P;
-            for (int j = 0; j < n; ++j) {
-                const int row = bottom ? j : (Ny - 1 - j);
-                const S v = STEP_A ? *cl_at(cl, sm, LP, Rs, Ny, G, b, row + ey)
-                                   : *cl_at(cl, sm, LP, Rs, Ny, G, bb, row);
-                acc += (double)ld_pop<S, C>(k, v, b);
-            }
-        }
-        return acc * k.inv_den;
-    };
-    const C pb = y < G ? C(wall(true)) : C(0);
-    const C pt = y >= Ny - G ? C(wall(false)) : C(0);
-    C f[V];
-#pragma unroll
-    for (int a = 0; a < V; ++a) {
-        const int ys = y - k.ey[a];
-        if (ys < 0) {
-            f[a] = pb * k.cw[a];
-        } else if (ys >= Ny) {
-            f[a] = pt * k.cw[a];
-        } else if (STEP_A) {
-            f[a] = ld_pop<S, C>(k, *cl_at(cl, sm, LP, Rs, Ny, G, a, y), a);
-        } else {
-            const int ab = a < R ? a : (a < R + P ? a + P : a - P);
-            f[a] = ld_pop<S, C>(k, *cl_at(cl, sm, LP, Rs, Ny, G, ab, ys), a);
-        }
-    }
-    const CellCoef<C> q = res_collide<SET, N, C>(k, f);
-    unsigned rs = sr_seed<S, C>(seed + unsigned(slot) * 0x632be5abu, y);
-#pragma unroll
-    for (int a = 0; a < V; ++a) {
-        const S v = st_pop<S, C>(k, f[a], a, rs);
-        if (STEP_A)
-            *cl_at(cl, sm, LP, Rs, Ny, G, plane_opp<SET>(a), y) = v;
-        else
-            *cl_at(cl, sm, LP, Rs, Ny, G, a, y + k.ey[a]) = v;
-    }
-    res_emit<C>(B, q, y, emit);
-}
-
-// Cluster c (blocks c * kClusterCTAs ..) advances channel slots[c] by K (even)
-// steps; clusters beyond *count_p exit at once, all their blocks together.
-template <class SET, int N, typename S, typename C>
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kClusterThreads, 1)
-k_engine_cluster(const EngineSolve<C>* __restrict__ solves, const int* __restrict__ slots,
-                 const int* __restrict__ count_p, const int* __restrict__ off_p,
-                 const unsigned* __restrict__ seed_p, int K) {
-    namespace cg = cooperative_groups;
-    constexpr int V = SET::R + 2 * SET::P, G = set_maxey<SET>();
-    extern __shared__ __align__(16) unsigned char cl_smem[];
-    S* const sm = reinterpret_cast<S*>(cl_smem);
-    cg::cluster_group cl = cg::this_cluster();
-    const int cid = blockIdx.x / kClusterCTAs;
-    if (cid >= *count_p) return;                      // uniform over the cluster
-    const int q = int(cl.block_rank());
-    const int slot = slots[*off_p + cid];
-    const EngineSolve<C>& B = solves[slot];
-    const int Ny = B.k.Ny;
-    const int Rs = (Ny + kClusterCTAs - 1) / kClusterCTAs;
-    const int LP = Rs + 2 * G;
-    const int y0 = q * Rs, y1 = min(y0 + Rs, Ny);
-    S* const sloc = sm - y0;                          // global row y at local row y - y0 (+ G)
-    const long long plane = B.k.plane;
-    // load the own rows into the opposite planes, as an A step leaves them
-    {
-        const S* src = static_cast<const S*>(B.f[B.phase]);
-        for (int y = y0 + threadIdx.x; y < y1; y += kClusterThreads)
-#pragma unroll
-            for (int a = 0; a < V; ++a) sloc[plane_opp<SET>(a) * LP + y + G] = src[a * plane + y];
-    }
-    cl.sync();                                        // every block started and loaded
-    const unsigned seed0 = *seed_p;
-#pragma unroll 1
-    for (int i = 0; i < K; ++i) {
-        const unsigned seed = seed0 + unsigned(i & 1);
-        const int emit = i == K - 1 ? 1 : (i == K - 2 ? 2 : 0);
-#pragma unroll 1
-        for (int y = y0 + threadIdx.x; y < y1; y += kClusterThreads) {
-            const bool local = (q == 0 || y - G >= y0) && (q == kClusterCTAs - 1 || y + G < y0 + Rs);
-            if (i & 1) {
-                if (local) res_node<SET, N, S, C, true>(B, sloc, LP, slot, y, seed, emit);
-                else res_node_cluster<SET, N, S, C, true>(B, sm, LP, Rs, slot, y, seed, emit);
-            } else {
-                if (local) res_node<SET, N, S, C, false>(B, sloc, LP, slot, y, seed, emit);
-                else res_node_cluster<SET, N, S, C, false>(B, sm, LP, Rs, slot, y, seed, emit);
-            }
-        }
-        cl.sync();
-    }
-    {
-        S* dst = static_cast<S*>(B.f[B.phase]);
-        for (int y = y0 + threadIdx.x; y < y1; y += kClusterThreads)
-#pragma unroll
-            for (int a = 0; a < V; ++a) dst[a * plane + y] = sloc[plane_opp<SET>(a) * LP + y + G];
     }
 }
 

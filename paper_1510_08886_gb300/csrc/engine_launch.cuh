@@ -116,69 +116,6 @@ int resident_attr_one(size_t smem) {
         default: break;                                                     \
     }
 
-struct ClusterLaunch {
-    const void* solves;        // EngineSolve<float>*
-    const int* slots;          // all cluster channels (each group's at its offset)
-    const int* count;          // device count of this group's cluster channels
-    const int* off;            // device offset of this group's cluster channels
-    const unsigned* seed;
-    int K;
-    int grid;                  // blocks, a multiple of kClusterCTAs
-    size_t smem;
-};
-
-template <class SET, int N, typename S>
-cudaError_t cluster_one(const ClusterLaunch& L, cudaStream_t st) {
-    k_engine_cluster<SET, N, S, float><<<L.grid, kClusterThreads, L.smem, st>>>(
-        static_cast<const EngineSolve<float>*>(L.solves), L.slots, L.count, L.off, L.seed, L.K);
-    return cudaGetLastError();
-}
-
-// Opt the cluster kernel of (set, N) into `smem` bytes of dynamic shared memory
-// and return how many of its clusters fit on the GPU at once (0: unusable).
-template <class SET, int N, typename S>
-int cluster_attr_one(size_t smem) {
-    const void* fn = reinterpret_cast<const void*>(&k_engine_cluster<SET, N, S, float>);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kClusterCTAs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(kClusterCTAs, 1, 1);
-    cfg.blockDim = dim3(kClusterThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_engine_cluster<SET, N, S, float>, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return n;
-}
-
-template <typename S>
-cudaError_t engine_cluster_t(int set_id, int N, const ClusterLaunch& L, cudaStream_t st) {
-#define LBM_CL_LAUNCH(SET, NN) cluster_one<SET, NN, S>(L, st)
-    LBM_RES_DISPATCH(LBM_CL_LAUNCH)
-#undef LBM_CL_LAUNCH
-    return cudaErrorInvalidValue;
-}
-
-template <typename S>
-int engine_cluster_attr_t(int set_id, int N, size_t smem) {
-#define LBM_CL_ATTR(SET, NN) cluster_attr_one<SET, NN, S>(smem)
-    LBM_RES_DISPATCH(LBM_CL_ATTR)
-#undef LBM_CL_ATTR
-    return 0;
-}
-
 template <typename S>
 cudaError_t engine_resident_t(int set_id, int N, const ResidentLaunch& L, cudaStream_t st) {
 #define LBM_RES_LAUNCH(SET, NN) resident_one<SET, NN, S>(L, st)

@@ -30,12 +30,6 @@ cudaError_t engine_resident_bf16(int set_id, int N, const ResidentLaunch& L, cud
 int engine_resident_attr_fp32(int set_id, int N, size_t smem);
 int engine_resident_attr_half(int set_id, int N, size_t smem);
 int engine_resident_attr_bf16(int set_id, int N, size_t smem);
-cudaError_t engine_cluster_fp32(int set_id, int N, const ClusterLaunch& L, cudaStream_t st);
-cudaError_t engine_cluster_half(int set_id, int N, const ClusterLaunch& L, cudaStream_t st);
-cudaError_t engine_cluster_bf16(int set_id, int N, const ClusterLaunch& L, cudaStream_t st);
-int engine_cluster_attr_fp32(int set_id, int N, size_t smem);
-int engine_cluster_attr_half(int set_id, int N, size_t smem);
-int engine_cluster_attr_bf16(int set_id, int N, size_t smem);
 cudaError_t engine_reduce(const void* solves, const int* active, double* out, int nslots,
                           cudaStream_t st);
 cudaError_t engine_advance(unsigned int* seed, unsigned int by, cudaStream_t st);
@@ -46,7 +40,6 @@ namespace {
 constexpr int kGroups = 18;        // 6 compiled velocity sets x Hermite orders 2..4
 constexpr int kMaxChunk = 1000;    // steps per captured chunk
 constexpr int kLanes = 4;          // concurrent streams inside a captured chunk
-constexpr int kClusterMinNy = 256; // one-column channels from this height may run on a cluster
 
 size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
 
@@ -115,11 +108,9 @@ SlotLayout slot_layout(int V, size_t ncell, size_t elem) {
 
 struct GroupWork {
     int g;
-    bool tiled, res, cl;   // the group has tiles / bundles / cluster channels
+    bool tiled, res;       // the group has tiles / bundles
     int grid, rgrid;       // persistent grids (set at capture)
-    bool operator==(const GroupWork& o) const {
-        return g == o.g && tiled == o.tiled && res == o.res && cl == o.cl;
-    }
+    bool operator==(const GroupWork& o) const { return g == o.g && tiled == o.tiled && res == o.res; }
 };
 
 struct EngSlot {
@@ -175,15 +166,10 @@ struct lbm_engine {
     lbm::ResChannel* d_chans = nullptr;        // max_slots entries
     int* d_nbundles = nullptr;                 // per group: counts, then offsets
     int* d_rcounters = nullptr;                // per group
-    // resident chunks of single channels on thread-block clusters
-    bool cluster = true;
-    int cl_occ[kGroups];                       // clusters that fit at once, -1: not yet queried
-    int* d_clslots = nullptr;                  // max_slots entries
-    int* d_ncl = nullptr;                      // per group: counts, then offsets
     cudaStream_t side[kLanes - 1] = {};        // forks of the chunk graph
     cudaEvent_t ev_fork = nullptr, ev_join[kLanes - 1] = {};
     std::vector<GroupWork> plan;               // present groups and their work
-    int n_tiled = 0, n_bundled = 0, n_cluster = 0;   // solves per path at the last rebuild
+    int n_tiled = 0, n_resident = 0;          // solves per path at the last rebuild
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -211,28 +197,6 @@ int res_occupancy(lbm_engine* e, int group) {
                                        : lbm::engine_resident_attr_fp32(set, N, e->res_smem);
     }
     return e->res_occ[group];
-}
-
-// dynamic shared memory of a cluster block: V planes of the largest slab
-// (ceil(kResNodes / kClusterCTAs) rows) plus the ghost rows
-size_t cl_smem(const lbm::SolveSpec& s) {
-    const size_t need = size_t(s.V) *
-                        ((lbm::kResNodes + lbm::kClusterCTAs - 1) / lbm::kClusterCTAs + 2 * s.maxey) *
-                        s.elem;
-    return std::max(need, size_t(120) << 10);   // above half an SM: one cluster block per SM
-}
-
-int cl_occupancy(lbm_engine* e, int group, const lbm::SolveSpec& s) {
-    if (e->cl_occ[group] < 0) {
-        const int set = group / 3, N = group % 3 + 2;
-        const size_t sm = cl_smem(s);
-        e->cl_occ[group] =
-            sm > e->res_smem ? 0
-            : e->precision == LBM_FP16 ? lbm::engine_cluster_attr_half(set, N, sm)
-            : e->precision == LBM_BF16 ? lbm::engine_cluster_attr_bf16(set, N, sm)
-                                       : lbm::engine_cluster_attr_fp32(set, N, sm);
-    }
-    return e->cl_occ[group];
 }
 
 // shared-memory footprint of a channel in a bundle: V planes of Nx (Ny + 2 maxey)
@@ -326,7 +290,6 @@ int rebuild_tiles(lbm_engine* e) {
     std::vector<lbm::ResChannel> chans;
     std::vector<GroupWork> plan;
     std::vector<int> counts(2 * kGroups, 0), nbund(2 * kGroups, 0);   // count, offset
-    std::vector<int> clslots, ncl(2 * kGroups, 0);
     for (int g = 0; g < kGroups; ++g) {
         const size_t start = t.size(), bstart = bundles.size();
         std::vector<int> res;
@@ -340,23 +303,6 @@ int rebuild_tiles(lbm_engine* e) {
             const int n = sl.spec.Nx * sl.spec.Ny;
             for (int c0 = 0; c0 < n; c0 += lbm::kBlock) t.push_back({s, c0});
         }
-        // few resident channels: the tall one-column ones run on clusters of
-        // kClusterCTAs SMs each (the grid has sms / kClusterCTAs clusters)
-        const size_t cstart = clslots.size();
-        if (e->cluster && !res.empty() && int(res.size()) * lbm::kClusterCTAs <= e->sms &&
-            cl_occupancy(e, g, e->slots[res[0]].spec) > 0) {
-            std::vector<int> keep;
-            for (int s : res) {
-                const lbm::SolveSpec& sp = e->slots[s].spec;
-                if (sp.Nx == 1 && sp.Ny >= kClusterMinNy)
-                    clslots.push_back(s);
-                else
-                    keep.push_back(s);
-            }
-            res.swap(keep);
-        }
-        ncl[g] = int(clslots.size() - cstart);
-        ncl[kGroups + g] = int(cstart);
         std::vector<ResItem> items;
         for (int s : res)
             items.push_back({res_bytes(e->slots[s].spec),
@@ -379,14 +325,7 @@ int rebuild_tiles(lbm_engine* e) {
         counts[kGroups + g] = int(start);
         nbund[g] = int(bundles.size() - bstart);
         nbund[kGroups + g] = int(bstart);
-        // the captured launches depend only on whether a group has tiles and
-        // whether it has resident solves (bundled or clustered: both resident
-        // kernels are launched, an empty list exits at once), so solves moving
-        // between bundles and clusters need no new capture
-        const bool cl_ok = e->cluster && (nbund[g] || ncl[g]) && cl_occupancy(e, g, e->slots[
-            ncl[g] ? clslots[cstart] : chans[bundles[bstart].first].slot].spec) > 0;
-        if (counts[g] || nbund[g] || ncl[g])
-            plan.push_back({g, counts[g] > 0, nbund[g] > 0 || ncl[g] > 0, cl_ok, 0, 0});
+        if (counts[g] || nbund[g]) plan.push_back({g, counts[g] > 0, nbund[g] > 0, 0, 0});
     }
     if (t.size() > e->tile_cap || bundles.size() > size_t(e->max_slots)) return LBM_ENOMEM;
     cudaError_t err = cudaSuccess;
@@ -405,18 +344,12 @@ int rebuild_tiles(lbm_engine* e) {
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(e->d_nbundles, nbund.data(), 2 * kGroups * sizeof(int),
                               cudaMemcpyHostToDevice, e->stream);
-    if (err == cudaSuccess && !clslots.empty())
-        err = cudaMemcpyAsync(e->d_clslots, clslots.data(), clslots.size() * sizeof(int),
-                              cudaMemcpyHostToDevice, e->stream);
-    if (err == cudaSuccess)
-        err = cudaMemcpyAsync(e->d_ncl, ncl.data(), 2 * kGroups * sizeof(int),
-                              cudaMemcpyHostToDevice, e->stream);
+
     if (err != cudaSuccess) return cuda_rc(err);
-    e->n_cluster = int(clslots.size());
-    e->n_bundled = int(chans.size());
+    e->n_resident = int(chans.size());
     e->n_tiled = 0;
     for (const EngSlot& sl : e->slots) e->n_tiled += sl.used;
-    e->n_tiled -= e->n_cluster + e->n_bundled;
+    e->n_tiled -= e->n_resident;
     // the graph reads counts and offsets from device memory: only a change of
     // the launches themselves needs a new capture
     if (!(plan == e->plan)) {
@@ -434,15 +367,14 @@ int rebuild_tiles(lbm_engine* e) {
 // so they overlap on the GPU and one group's kernel tail is filled by
 // another's blocks.  Items are dealt to kLanes streams in order.
 int enqueue_chunk(lbm_engine* e) {
-    bool any_t = false, any_r = false, any_c = false;
+    bool any_t = false, any_r = false;
     int items = 0;
     for (const GroupWork& w : e->plan) {
         any_t |= w.tiled;
         any_r |= w.res;
-        any_c |= w.cl;
         items += w.tiled;
     }
-    items += any_r + any_c;
+    items += any_r;
     cudaError_t err = cudaSuccess;
     if (any_t) err = cudaMemsetAsync(e->d_counters, 0, sizeof(int) * kGroups * e->K, e->stream);
     if (any_r && err == cudaSuccess)
@@ -476,29 +408,6 @@ int enqueue_chunk(lbm_engine* e) {
             err = e->precision == LBM_FP16   ? lbm::engine_resident_half(set, N, L, rs)
                   : e->precision == LBM_BF16 ? lbm::engine_resident_bf16(set, N, L, rs)
                                              : lbm::engine_resident_fp32(set, N, L, rs);
-            if (err != cudaSuccess) return cuda_rc(err);
-        }
-    }
-    if (any_c) {
-        const cudaStream_t cs = lane(item++);
-        for (const GroupWork& w : e->plan) {
-            if (!w.cl) continue;
-            lbm::ClusterLaunch L{};
-            L.solves = e->d_solves;
-            L.slots = e->d_clslots;
-            L.count = e->d_ncl + w.g;
-            L.off = e->d_ncl + kGroups + w.g;
-            L.seed = e->d_seed;
-            L.K = e->K;
-            L.grid = (e->sms / lbm::kClusterCTAs) * lbm::kClusterCTAs;
-            const int set = w.g / 3, N = w.g % 3 + 2;
-            lbm::SolveSpec sp;
-            for (const EngSlot& sl : e->slots)
-                if (sl.used && sl.group == w.g) { sp = sl.spec; break; }
-            L.smem = cl_smem(sp);
-            err = e->precision == LBM_FP16   ? lbm::engine_cluster_half(set, N, L, cs)
-                  : e->precision == LBM_BF16 ? lbm::engine_cluster_bf16(set, N, L, cs)
-                                             : lbm::engine_cluster_fp32(set, N, L, cs);
             if (err != cudaSuccess) return cuda_rc(err);
         }
     }
@@ -617,8 +526,6 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
     const size_t o_rcounters = take(sizeof(int) * kGroups);
     const size_t o_bundles = take(sizeof(lbm::ResBundle) * max_solves);
     const size_t o_chans = take(sizeof(lbm::ResChannel) * max_solves);
-    const size_t o_clslots = take(sizeof(int) * max_solves);
-    const size_t o_ncl = take(sizeof(int) * 2 * kGroups);
     const size_t o_counters = take(sizeof(int) * kGroups * kMaxChunk);
     const size_t o_seed = take(sizeof(unsigned));
     const size_t o_tiles = take(sizeof(lbm::EngineTile) * e->tile_cap);
@@ -641,9 +548,7 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
     e->d_rcounters = reinterpret_cast<int*>(e->base + o_rcounters);
     e->d_bundles = reinterpret_cast<lbm::ResBundle*>(e->base + o_bundles);
     e->d_chans = reinterpret_cast<lbm::ResChannel*>(e->base + o_chans);
-    e->d_clslots = reinterpret_cast<int*>(e->base + o_clslots);
-    e->d_ncl = reinterpret_cast<int*>(e->base + o_ncl);
-    for (int g = 0; g < kGroups; ++g) e->res_occ[g] = e->cl_occ[g] = -1;
+    for (int g = 0; g < kGroups; ++g) e->res_occ[g] = -1;
     e->d_counters = reinterpret_cast<int*>(e->base + o_counters);
     e->d_seed = reinterpret_cast<unsigned*>(e->base + o_seed);
     e->d_tiles = reinterpret_cast<lbm::EngineTile*>(e->base + o_tiles);
@@ -801,22 +706,12 @@ int lbm_engine_set_resident(lbm_engine* e, int enable) {
     return LBM_OK;
 }
 
-int lbm_engine_paths(lbm_engine* e, int* tiled, int* bundled, int* clustered) {
+int lbm_engine_paths(lbm_engine* e, int* tiled, int* resident) {
     if (!e) return LBM_EINVAL;
     const int rc = prepare(e);
     if (rc) return rc;
     if (tiled) *tiled = e->n_tiled;
-    if (bundled) *bundled = e->n_bundled;
-    if (clustered) *clustered = e->n_cluster;
-    return LBM_OK;
-}
-
-int lbm_engine_set_cluster(lbm_engine* e, int enable) {
-    if (!e || (enable != 0 && enable != 1)) return LBM_EINVAL;
-    if (e->cluster != (enable == 1)) {
-        e->cluster = enable == 1;
-        e->tiles_dirty = true;
-    }
+    if (resident) *resident = e->n_resident;
     return LBM_OK;
 }
 

@@ -124,17 +124,36 @@ __device__ __forceinline__ S st_pop(const KParams<C>& k, C v, int a, unsigned& r
     }
 }
 
+// fp64 sum of the wall terms in a fixed order: term k goes to accumulator
+// k mod 4, the four are combined as (a0 + a1) + (a2 + a3).  Four interleaved
+// chains instead of one keep the fp64 latency of a wall node short; every
+// kernel uses this order, so all paths give the same bits.
+struct Acc4 {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    __device__ __forceinline__ void add(int k, double v) {
+        switch (k & 3) {
+            case 0: a0 += v; break;
+            case 1: a1 += v; break;
+            case 2: a2 += v; break;
+            default: a3 += v; break;
+        }
+    }
+    __device__ __forceinline__ double sum() const { return (a0 + a1) + (a2 + a3); }
+};
+
 // Wall flux balance (Eq. nm.15) for landing column x, in deviation form:
 // returns dPsi = sum_out d_b / sum_in |e_y| w  so that an unknown incoming
 // population is d_a = dPsi * w_a, i.e. fbar_a = Psi rho_w w_a (Eq. nm.14).
 // Outgoing populations b (e_y < 0 at the bottom wall, e_y > 0 at the top)
 // cross the wall from their |e_y| rows nearest to it and are credited to the
-// column they land on, so the source column is x - e_x.  fp64 accumulation in
-// every precision; the fill d_a = dPsi w_a is formed in the compute type.
+// column they land on, so the source column is x - e_x.  Terms in plane order,
+// nearest row first; fp64 accumulation (Acc4) in every precision; the fill
+// d_a = dPsi w_a is formed in the compute type.
 template <typename S, typename C>
 __device__ __noinline__ double wall_dpsi(const KParams<C>& k, const S* __restrict__ src, int x,
-                                    bool bottom) {
-    double acc = 0.0;
+                                         bool bottom) {
+    Acc4 acc;
+    int t = 0;
     for (int b = k.R; b < k.V; ++b) {
         const int ey = k.ey[b];
         if (bottom ? (ey >= 0) : (ey <= 0)) continue;
@@ -144,10 +163,56 @@ __device__ __noinline__ double wall_dpsi(const KParams<C>& k, const S* __restric
         const S* pl = src + (long long)b * k.plane + xs;
         for (int j = 0; j < n; ++j) {
             const int row = bottom ? j : (k.Ny - 1 - j);
-            acc += (double)ld_pop<S, C>(k, pl[(long long)row * k.Nx], b);
+            acc.add(t++, (double)ld_pop<S, C>(k, pl[(long long)row * k.Nx], b));
         }
     }
-    return acc * k.inv_den;
+    return acc.sum() * k.inv_den;
+}
+
+// Number of wall terms of the planes before plane a of a compiled set.
+template <class SET, bool BOTTOM>
+__host__ __device__ constexpr int wall_terms_before(int a) {
+    int t = 0;
+    for (int b = 0; b < a; ++b) {
+        const int ey = b < SET::R ? 0 : (b < SET::R + SET::P ? SET::ey[b - SET::R] : -SET::ey[b - SET::R - SET::P]);
+        if (BOTTOM ? ey < 0 : ey > 0) t += BOTTOM ? -ey : ey;
+    }
+    return t;
+}
+
+// The same sum for a compiled set, unrolled: term(plane, j) gives the
+// outgoing population of plane `plane` (an integral_constant) that crossed
+// from the j-th row off the wall.
+template <class SET, bool BOTTOM, int A, class TERM>
+__device__ __forceinline__ void wall_add_plane(Acc4& acc, const TERM& term) {
+    constexpr int ey = A < SET::R ? 0 : (A < SET::R + SET::P ? SET::ey[A - SET::R] : -SET::ey[A - SET::R - SET::P]);
+    if constexpr (BOTTOM ? ey < 0 : ey > 0) {
+        constexpr int n = BOTTOM ? -ey : ey;
+        constexpr int t0 = wall_terms_before<SET, BOTTOM>(A);
+#pragma unroll
+        for (int j = 0; j < n; ++j) acc.add(t0 + j, term(std::integral_constant<int, A>{}, j));
+    }
+}
+
+template <class SET, bool BOTTOM, class TERM, int... I>
+__device__ __forceinline__ double wall_sum_ct(const TERM& term, std::integer_sequence<int, I...>) {
+    Acc4 acc;
+    (wall_add_plane<SET, BOTTOM, I>(acc, term), ...);
+    return acc.sum();
+}
+
+// Wall balance of a compiled set on a lattice in device memory.
+template <class SET, typename S, typename C, bool BOTTOM>
+__device__ __forceinline__ double wall_dpsi_ct(const KParams<C>& k, const S* __restrict__ src, int x) {
+    constexpr int V = SET::R + 2 * SET::P;
+    auto term = [&](auto bc, int j) {
+        constexpr int b = decltype(bc)::value;
+        int xs = x - k.sx[b];
+        xs += (xs < 0) ? k.Nx : 0;
+        const int row = BOTTOM ? j : (k.Ny - 1 - j);
+        return (double)ld_pop<S, C>(k, src[(long long)b * k.plane + (long long)row * k.Nx + xs], b);
+    };
+    return wall_sum_ct<SET, BOTTOM>(term, std::make_integer_sequence<int, V>{}) * k.inv_den;
 }
 
 // Per-node coefficients of the relaxation target, from the deviation moments
@@ -273,6 +338,26 @@ __device__ __forceinline__ C pull(const KParams<C>& k, const S* __restrict__ src
     int xs = x - k.sx[a];
     xs += (xs < 0) ? k.Nx : 0;
     return ld_pop<S, C>(k, src[(long long)a * k.plane + (long long)(y - k.ey[a]) * k.Nx + xs], a);
+}
+
+// Populations of a wall node of a compiled set: the fill for those whose
+// source lies beyond a wall, the pull for the others.
+template <class SET, typename S, typename C, int A>
+__device__ __forceinline__ C wall_value(const KParams<C>& k, const S* __restrict__ src, int x, int y,
+                                        C pb, C pt) {
+    constexpr int EY = A < SET::R ? 0 : (A < SET::R + SET::P ? SET::ey[A - SET::R] : -SET::ey[A - SET::R - SET::P]);
+    const int ys = y - EY;
+    if (ys < 0) return pb * k.cw[A];
+    if (ys >= k.Ny) return pt * k.cw[A];
+    return pull<S, C>(k, src, A, x, y);
+}
+
+template <class SET, typename S, typename C, int... I>
+__device__ __forceinline__ void pull_wall_ct(const KParams<C>& k, const S* __restrict__ src, int x,
+                                             int y, C* f, std::integer_sequence<int, I...>) {
+    const C pb = y < k.maxey ? C(wall_dpsi_ct<SET, S, C, true>(k, src, x)) : C(0);
+    const C pt = y >= k.Ny - k.maxey ? C(wall_dpsi_ct<SET, S, C, false>(k, src, x)) : C(0);
+    ((f[I] = wall_value<SET, S, C, I>(k, src, x, y, pb, pt)), ...);
 }
 
 // ---- compile-time velocity sets ---------------------------------------------
@@ -454,22 +539,10 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
         const int y = cell / k.Nx;
         const int x = cell - y * k.Nx;
         const bool nb = y < k.maxey, nt = y >= k.Ny - k.maxey;
-        if (!nb && !nt) {          // a node away from the walls in a tile that touches one
+        if (!nb && !nt)            // a node away from the walls in a tile that touches one
             pull_rows_any<SET, S, C>(k, k.srcf, cell, f);
-        } else {
-        const C pb = nb ? C(wall_dpsi<S, C>(k, src, x, true)) : C(0);
-        const C pt = nt ? C(wall_dpsi<S, C>(k, src, x, false)) : C(0);
-#pragma unroll
-        for (int a = 0; a < V; ++a) {
-            const int ys = y - k.ey[a];
-            if (ys < 0)
-                f[a] = pb * k.cw[a];
-            else if (ys >= k.Ny)
-                f[a] = pt * k.cw[a];
-            else
-                f[a] = pull<S, C>(k, src, a, x, y);
-        }
-        }
+        else
+            pull_wall_ct<SET, S, C>(k, src, x, y, f, std::make_integer_sequence<int, V>{});
     }
     C drho = R ? f[0] : C(0), Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
     moments_ct<SET, C>(f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, P>{});
