@@ -343,7 +343,7 @@ class Engine:
             ctypes.c_void_p(stream.cuda_stream) if stream is not None else None, ctypes.byref(h)),
             "lbm_engine_create")
         self._h = h
-        self._dvms = {}
+        self._dvm_cache = {}
         self.results = np.zeros((self.max_solves, 4))
         self.set_chunk(chunk)
         self.set_resident(resident)
@@ -383,8 +383,19 @@ class Engine:
               "lbm_engine_paths")
         return t.value, r.value
 
+    def _dvm(self, e, w, c):
+        """The lbm_dvm of a velocity set, built once per distinct set (the
+        library copies it at each add)."""
+        e = np.asarray(e, dtype=np.int32)
+        w = np.asarray(w, dtype=np.float64)
+        key = (e.tobytes(), w.tobytes(), float(c))
+        d = self._dvm_cache.get(key)
+        if d is None:
+            d = self._dvm_cache[key] = _DVM(e, w, c)
+        return d
+
     def add(self, e, w, c, order, Nx, Ny, Kn, force, rho=None):
-        d = _DVM(e, w, c)
+        d = self._dvm(e, w, c)
         slot = ctypes.c_int(-1)
         r = None
         if rho is not None:
@@ -395,12 +406,10 @@ class Engine:
         if rc == _lib.LBM_ENOMEM:
             return None
         check(rc, "lbm_engine_add")
-        self._dvms[slot.value] = d
         return slot.value
 
     def remove(self, slot):
         check(_lib.lib().lbm_engine_remove(self._h, int(slot)), "lbm_engine_remove")
-        self._dvms.pop(slot, None)
 
     def run(self, chunks=1):
         """Advance every resident solve by chunks x chunk steps; returns the

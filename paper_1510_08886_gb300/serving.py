@@ -112,7 +112,11 @@ class ContinuousBatcher:
         rejects (unknown velocity set, invalid arguments) is answered at once
         with its error code instead of stopping the server."""
         still = []
-        for r in self.queue:
+        cap = getattr(self.engine, "max_solves", None)
+        for i, r in enumerate(self.queue):
+            if cap is not None and len(self.active) >= cap:
+                still.extend(self.queue[i:])      # no free slot: the rest waits
+                break
             try:
                 e, w, c = self.sets[r.dvm]
                 slot = self.engine.add(e, w, c, r.order, r.Nx, r.Ny, r.Kn, r.force)
@@ -138,18 +142,24 @@ class ContinuousBatcher:
         self.chunks += 1
         self.cell_steps += sum(r.Nx * r.Ny for r in self.active.values()) * self.engine.chunk
         now = self.clock()
-        finished = []
-        for slot, r in self.active.items():
+        slots = np.fromiter(self.active.keys(), dtype=np.int64, count=len(self.active))
+        reqs = list(self.active.values())
+        for r in reqs:
             r.steps += self.engine.chunk          # every resident solve ran the chunk
-            steps = r.steps
-            du = float(res[slot, 0])
-            status = 0 if math.isfinite(du) else -5      # a non-finite state makes du NaN
-            if status != 0 or du < r.tol or steps >= self.max_steps:
-                r.status, r.du = status, du
-                r.converged = status == 0 and du < r.tol
-                r.mdot, r.us = float(res[slot, 1]), float(res[slot, 2])
-                r.t_done = now
-                finished.append(slot)
+        du = res[slots, 0]
+        tol = np.array([r.tol for r in reqs])
+        steps = np.array([r.steps for r in reqs])
+        # harvest: converged, out of steps, or non-finite (a non-finite state makes du NaN or inf)
+        done = ~(np.isfinite(du) & (du >= tol)) | (steps >= self.max_steps)
+        finished = []
+        for i in np.nonzero(done)[0]:
+            slot, r, d = int(slots[i]), reqs[i], float(du[i])
+            status = 0 if math.isfinite(d) else -5
+            r.status, r.du = status, d
+            r.converged = status == 0 and d < r.tol
+            r.mdot, r.us = float(res[slot, 1]), float(res[slot, 2])
+            r.t_done = now
+            finished.append(slot)
         for slot in finished:
             self.engine.remove(slot)
             self.done.append(self.active.pop(slot))

@@ -202,3 +202,33 @@ def test_failures_do_not_stop_the_server():
     assert by[2].status == -5 and not by[2].converged
     assert st.completed == 2 and st.extra["failed"] == 3
     assert all(s is None for s in eng.slots)          # every slot released
+
+
+def test_infinite_change_is_a_failure_and_full_slots_stop_admission():
+    """A solve whose per-step change is infinite is answered as non-finite;
+    with every slot taken, queued requests wait without being tried."""
+    clk = FakeClock()
+
+    class Inf(FakeEngine):
+        max_solves = 2
+        tries = 0
+
+        def add(self, *a):
+            Inf.tries += 1
+            return super().add(*a)
+
+        def run(self, chunks):
+            res = super().run(chunks)
+            for i, s in enumerate(self.slots):
+                if s and s["Ny"] == 19:
+                    res[i, 0] = math.inf
+            return res
+
+    eng = Inf(capacity=10**9, slots=2, clock=clk)
+    b = ContinuousBatcher(eng, SETS, clock=clk)
+    reqs = _reqs([(0.0, 19, 0.1, 1e-6), (0.0, 64, 0.1, 1e-6)] + [(0.0, 32, 0.1, 1e-6)] * 6)
+    st = b.serve(reqs, realtime=False)
+    by = {r.rid: r for r in b.done}
+    assert by[0].status == -5 and not by[0].converged
+    assert st.completed == 7 and st.extra["failed"] == 1
+    assert Inf.tries == len(reqs)          # each request tried once: no retries while full
