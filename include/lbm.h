@@ -302,6 +302,21 @@ int lbm_engine_paths(lbm_engine* e, int* tiled, int* resident);
  * <u_x>; entries of free slots are stale.  Synchronises. */
 int lbm_engine_run(lbm_engine* e, int chunks, double* results);
 
+/* Asynchronous form of lbm_engine_run, so that the host can prepare the next
+ * chunk while the GPU runs this one.  lbm_engine_launch queues chunks * K
+ * steps (with the solves resident at the call) and an in-stream copy of the
+ * per-slot results after them into pinned host memory, and returns at once;
+ * lbm_engine_wait waits for the oldest outstanding launch and copies its
+ * results (layout as lbm_engine_run) to `results` (may be NULL).  At most two
+ * launches may be outstanding (LBM_EINVAL otherwise, and for a wait with none
+ * outstanding).  Adding or removing solves between a launch and its wait is
+ * allowed and stream-ordered: a removed solve is still advanced by the
+ * launches queued before its removal, and results of a slot refer to the
+ * solve it held when that launch was queued.  lbm_engine_run and
+ * lbm_engine_autotune return LBM_EINVAL while launches are outstanding. */
+int lbm_engine_launch(lbm_engine* e, int chunks);
+int lbm_engine_wait(lbm_engine* e, double* results);
+
 /* Time candidate launch shapes (fraction of the occupancy limit used for the
  * persistent grid x tiles taken per grab) on the resident solves and keep
  * the fastest.  The timed chunks advance the solves (3 chunks per candidate,

@@ -417,6 +417,16 @@ class Engine:
         check(_lib.lib().lbm_engine_run(self._h, int(chunks), _dp(self.results)), "lbm_engine_run")
         return self.results
 
+    def launch(self, chunks=1):
+        """Queue chunks x chunk steps and return at once (at most two
+        launches outstanding); collect their results with ``wait``."""
+        check(_lib.lib().lbm_engine_launch(self._h, int(chunks)), "lbm_engine_launch")
+
+    def wait(self):
+        """Results of the oldest outstanding launch (the array ``run`` returns)."""
+        check(_lib.lib().lbm_engine_wait(self._h, _dp(self.results)), "lbm_engine_wait")
+        return self.results
+
     def autotune(self):
         ms = ctypes.c_double(0)
         check(_lib.lib().lbm_engine_autotune(self._h, ctypes.byref(ms)), "lbm_engine_autotune")

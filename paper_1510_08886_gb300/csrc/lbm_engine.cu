@@ -153,6 +153,11 @@ struct lbm_engine {
     std::vector<lbm::EngineSolve<float>> h_solves;
     std::vector<int> h_active;
     std::vector<double> h_results;
+    // asynchronous chunks: per outstanding launch, its results copied in
+    // stream order into pinned host memory, and an event marking the copy
+    double* pinned = nullptr;                  // 2 x 4 x max_slots doubles
+    cudaEvent_t ev_done[2] = {};
+    int pending = 0, head = 0;                 // outstanding launches, oldest one
     int K = 100;
     double bps_factor = 1.0;   // fraction of the occupancy limit used for the grid
     int grab = 4;              // tiles taken per atomic grab
@@ -556,6 +561,11 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
     e->h_solves.resize(max_solves);
     e->h_active.assign(max_solves, 0);
     e->h_results.assign(4 * size_t(max_solves), 0.0);
+    if (cudaMallocHost(&e->pinned, sizeof(double) * 8 * size_t(max_solves)) != cudaSuccess) {
+        cudaGetLastError();
+        lbm_engine_destroy(e);
+        return LBM_ENOMEM;
+    }
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err == cudaSuccess) err = cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -569,6 +579,8 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
         if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->ev_join[l], cudaEventDisableTiming);
     }
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming);
+    for (int l = 0; l < 2 && err == cudaSuccess; ++l)
+        err = cudaEventCreateWithFlags(&e->ev_done[l], cudaEventDisableTiming);
     if (err == cudaSuccess) {
         if (stream) {
             e->stream = static_cast<cudaStream_t>(stream);
@@ -592,6 +604,9 @@ void lbm_engine_destroy(lbm_engine* e) {
     if (e->stream) cudaStreamSynchronize(e->stream);
     if (e->exec) cudaGraphExecDestroy(e->exec);
     if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+    for (int l = 0; l < 2; ++l)
+        if (e->ev_done[l]) cudaEventDestroy(e->ev_done[l]);
+    if (e->pinned) cudaFreeHost(e->pinned);
     for (int l = 0; l < kLanes - 1; ++l) {
         if (e->ev_join[l]) cudaEventDestroy(e->ev_join[l]);
         if (e->side[l]) cudaStreamDestroy(e->side[l]);
@@ -724,8 +739,43 @@ int lbm_engine_set_chunk(lbm_engine* e, int steps) {
     return LBM_OK;
 }
 
+int lbm_engine_launch(lbm_engine* e, int chunks) {
+    if (!e || chunks < 0 || e->pending >= 2) return LBM_EINVAL;
+    int rc = prepare(e);
+    if (rc) return rc;
+    if (!e->plan.empty()) {
+        for (int c = 0; c < chunks; ++c) {
+            const cudaError_t err = cudaGraphLaunch(e->exec, e->stream);
+            if (err != cudaSuccess) return cuda_rc(err);
+        }
+        for (auto& sl : e->slots)
+            if (sl.used) sl.steps += long(chunks) * e->K;
+    }
+    const int b = (e->head + e->pending) & 1;
+    cudaError_t err = cudaMemcpyAsync(e->pinned + size_t(b) * 4 * e->max_slots, e->d_results,
+                                      sizeof(double) * 4 * e->max_slots, cudaMemcpyDeviceToHost,
+                                      e->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(e->ev_done[b], e->stream);
+    if (err != cudaSuccess) return cuda_rc(err);
+    ++e->pending;
+    return LBM_OK;
+}
+
+int lbm_engine_wait(lbm_engine* e, double* results) {
+    if (!e || e->pending == 0) return LBM_EINVAL;
+    const int b = e->head;
+    const cudaError_t err = cudaEventSynchronize(e->ev_done[b]);
+    if (err != cudaSuccess) return cuda_rc(err);
+    if (results)
+        std::memcpy(results, e->pinned + size_t(b) * 4 * e->max_slots,
+                    sizeof(double) * 4 * e->max_slots);
+    e->head ^= 1;
+    --e->pending;
+    return LBM_OK;
+}
+
 int lbm_engine_run(lbm_engine* e, int chunks, double* results) {
-    if (!e || chunks < 0) return LBM_EINVAL;
+    if (!e || chunks < 0 || e->pending) return LBM_EINVAL;
     int rc = prepare(e);
     if (rc) return rc;
     if (!e->plan.empty()) {
@@ -740,7 +790,7 @@ int lbm_engine_run(lbm_engine* e, int chunks, double* results) {
 }
 
 int lbm_engine_autotune(lbm_engine* e, double* best_ms_per_step) {
-    if (!e) return LBM_EINVAL;
+    if (!e || e->pending) return LBM_EINVAL;
     int rc = prepare(e);
     if (rc) return rc;
     if (e->plan.empty()) return LBM_OK;

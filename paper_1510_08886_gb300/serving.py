@@ -90,7 +90,7 @@ def _stats(done, t0, t1, max_resident, chunks, cell_steps):
 
 class ContinuousBatcher:
     """Drive an engine (paper_1510_08886_gb300.Engine, or any object with
-    add/remove/run/info/chunk) with a request queue."""
+    add/remove/run/chunk, and optionally launch/wait) with a request queue."""
 
     def __init__(self, engine, velocity_sets, max_steps=200000, clock=time.perf_counter):
         self.engine = engine
@@ -103,6 +103,7 @@ class ContinuousBatcher:
         self.chunks = 0
         self.cell_steps = 0.0
         self.max_resident = 0
+        self._inflight = []                # snapshots of launched, unharvested chunks
 
     def submit(self, req):
         self.queue.append(req)
@@ -133,29 +134,34 @@ class ContinuousBatcher:
         self.queue = still
         self.max_resident = max(self.max_resident, len(self.active))
 
-    def step(self):
-        """Admit, advance every resident solve by one chunk, harvest."""
-        self.admit()
-        if not self.active:
-            return 0
-        res = self.engine.run(1)
+    def _launch_snapshot(self):
+        """Count one chunk for every resident solve; return (slot, request,
+        steps after the chunk) for the harvest of that chunk's results."""
         self.chunks += 1
         self.cell_steps += sum(r.Nx * r.Ny for r in self.active.values()) * self.engine.chunk
+        snap = []
+        for slot, r in self.active.items():
+            r.steps += self.engine.chunk
+            snap.append((slot, r, r.steps))
+        return snap
+
+    def _harvest(self, res, snap):
+        """Retire the solves of a finished chunk whose result meets their
+        tolerance, ran out of steps or turned non-finite (du NaN or inf)."""
+        live = [(s, r, st) for s, r, st in snap if self.active.get(s) is r]
+        if not live:
+            return 0
         now = self.clock()
-        slots = np.fromiter(self.active.keys(), dtype=np.int64, count=len(self.active))
-        reqs = list(self.active.values())
-        for r in reqs:
-            r.steps += self.engine.chunk          # every resident solve ran the chunk
+        slots = np.array([s for s, _, _ in live], dtype=np.int64)
         du = res[slots, 0]
-        tol = np.array([r.tol for r in reqs])
-        steps = np.array([r.steps for r in reqs])
-        # harvest: converged, out of steps, or non-finite (a non-finite state makes du NaN or inf)
+        tol = np.array([r.tol for _, r, _ in live])
+        steps = np.array([st for _, _, st in live])
         done = ~(np.isfinite(du) & (du >= tol)) | (steps >= self.max_steps)
         finished = []
         for i in np.nonzero(done)[0]:
-            slot, r, d = int(slots[i]), reqs[i], float(du[i])
+            slot, r, d = int(slots[i]), live[i][1], float(du[i])
             status = 0 if math.isfinite(d) else -5
-            r.status, r.du = status, d
+            r.status, r.du, r.steps = status, d, int(steps[i])
             r.converged = status == 0 and d < r.tol
             r.mdot, r.us = float(res[slot, 1]), float(res[slot, 2])
             r.t_done = now
@@ -165,6 +171,30 @@ class ContinuousBatcher:
             self.done.append(self.active.pop(slot))
         return len(finished)
 
+    def step(self):
+        """Admit, advance every resident solve by one chunk, harvest.
+
+        With an engine that can launch asynchronously (launch/wait), the
+        next chunk is queued before the previous one's results are
+        processed, so the GPU runs while the host harvests and admits: a
+        solve is harvested from the results of the chunk that met its
+        tolerance (its reported steps are that chunk's), it has already
+        been queued for one more chunk by then, and an admitted request
+        joins one chunk later."""
+        self.admit()
+        if not hasattr(self.engine, "launch"):
+            if not self.active:
+                return 0
+            res = self.engine.run(1)
+            return self._harvest(res, self._launch_snapshot())
+        if self.active:
+            self.engine.launch(1)
+            self._inflight.append(self._launch_snapshot())
+        if self._inflight and (len(self._inflight) == 2 or not self.active):
+            res = self.engine.wait()
+            return self._harvest(res, self._inflight.pop(0))
+        return 0
+
     def serve(self, requests, realtime=True, time_limit=None):
         """Play a request stream (t_arrival relative to the start) and return
         ServeStats.  With realtime=False, arrival times are ignored (every
@@ -172,7 +202,7 @@ class ContinuousBatcher:
         pending = sorted(requests, key=lambda r: r.t_arrival)
         t0 = self.clock()
         i = 0
-        while i < len(pending) or self.queue or self.active:
+        while i < len(pending) or self.queue or self.active or self._inflight:
             now = self.clock()
             if time_limit is not None and now - t0 > time_limit:
                 break
@@ -181,7 +211,7 @@ class ContinuousBatcher:
                 r.t_arrival = t0 + r.t_arrival if realtime else t0
                 self.submit(r)
                 i += 1
-            if not self.queue and not self.active and i < len(pending):
+            if not self.queue and not self.active and not self._inflight and i < len(pending):
                 time.sleep(max(0.0, min(0.01, pending[i].t_arrival - (self.clock() - t0))))
                 continue
             self.step()

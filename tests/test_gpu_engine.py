@@ -279,3 +279,38 @@ def test_engine_checkpoint_restores_bitwise():
                                            bad.nbytes) == _lib.LBM_EINVAL
     a.close()
     b.close()
+
+
+def test_launch_wait_equals_run():
+    """Asynchronous chunks give the results of the synchronous ones, chunk
+    by chunk; run, autotune and a third launch are refused while launches
+    are outstanding; a solve removed between launch and wait still gets the
+    queued chunk."""
+    import paper_1510_08886_gb300 as lbm
+    from paper_1510_08886_gb300 import _lib
+    a = lbm.Engine("fp32", max_solves=8, arena_bytes=128 << 20, chunk=10)
+    b = lbm.Engine("fp32", max_solves=8, arena_bytes=128 << 20, chunk=10)
+    sa = [_add(a, s, seed=41 + i) for i, s in enumerate(MIX[:5])]
+    sb = [_add(b, s, seed=41 + i) for i, s in enumerate(MIX[:5])]
+    ra = [a.run(1).copy() for _ in range(3)]
+    b.launch(1)
+    b.launch(1)
+    assert _lib.lib().lbm_engine_launch(b._h, 1) == _lib.LBM_EINVAL
+    assert _lib.lib().lbm_engine_run(b._h, 1, None) == _lib.LBM_EINVAL
+    assert _lib.lib().lbm_engine_autotune(b._h, None) == _lib.LBM_EINVAL
+    rb = [b.wait().copy()]
+    b.launch(1)
+    rb += [b.wait().copy(), b.wait().copy()]
+    assert _lib.lib().lbm_engine_wait(b._h, None) == _lib.LBM_EINVAL
+    for x, y in zip(ra, rb):
+        for s1, s2 in zip(sa, sb):
+            assert np.array_equal(x[s1], y[s2])
+    # removal between launch and wait: the removed solve's result is that chunk's
+    a.run(1)
+    b.launch(1)
+    b.remove(sb[0])
+    rb4 = b.wait().copy()
+    ra4 = a.results.copy()
+    assert np.array_equal(ra4[sa[0]], rb4[sb[0]])
+    a.close()
+    b.close()

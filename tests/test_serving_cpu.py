@@ -232,3 +232,67 @@ def test_infinite_change_is_a_failure_and_full_slots_stop_admission():
     assert by[0].status == -5 and not by[0].converged
     assert st.completed == 7 and st.extra["failed"] == 1
     assert Inf.tries == len(reqs)          # each request tried once: no retries while full
+
+
+class PipeFake(FakeEngine):
+    """FakeEngine with asynchronous chunks: a launch computes that chunk's
+    results (the state after it), a wait hands them back oldest first."""
+
+    def __init__(self, *a, **k):
+        super().__init__(*a, **k)
+        self.q = []
+
+    def launch(self, chunks):
+        assert len(self.q) < 2
+        self.q.append(self.run(chunks).copy())
+
+    def wait(self):
+        return self.q.pop(0)
+
+
+def test_pipelined_chunks_give_the_same_answers():
+    """Launching chunk k + 1 before harvesting chunk k: every request is
+    answered from the chunk that met its tolerance, with the same step count
+    and results as the synchronous loop (all requests admitted at once)."""
+    specs = [(0.0, ny, kn, tol) for ny, kn, tol in
+             [(64, 0.1, 1e-6), (128, 0.5, 1e-8), (32, 0.01, 1e-6), (200, 0.3, 1e-7),
+              (16, 1.0, 1e-6), (90, 0.05, 1e-8)]]
+    out = {}
+    for cls in (FakeEngine, PipeFake):
+        clk = FakeClock()
+        eng = cls(capacity=10**9, slots=8, clock=clk)
+        b = ContinuousBatcher(eng, SETS, clock=clk)
+        st = b.serve(_reqs(specs), realtime=False)
+        assert st.completed == len(specs)
+        assert all(s is None for s in eng.slots)
+        out[cls] = {r.rid: (r.steps, r.mdot, r.converged) for r in b.done}
+    assert out[FakeEngine] == out[PipeFake]
+
+
+def test_pipelined_slot_reuse_and_failures():
+    """A slot freed by a harvest and taken by a new request while the next
+    chunk (still holding the old solve) is in flight: the old solve's stale
+    row is skipped; non-finite solves are answered with their status."""
+    clk = FakeClock()
+
+    class P(PipeFake):
+        def run(self, chunks):
+            res = super().run(chunks)
+            for i, s in enumerate(self.slots):
+                if s and s["Ny"] == 17:
+                    res[i, 0] = math.nan
+            return res
+
+    eng = P(capacity=10**9, slots=2, clock=clk)
+    b = ContinuousBatcher(eng, SETS, clock=clk)
+    reqs = _reqs([(0.0, 16, 0.01, 1e-3), (0.0, 17, 0.1, 1e-6)] + [(0.0, 20 + i, 0.02, 1e-6)
+                                                                    for i in range(5)])
+    st = b.serve(reqs, realtime=False)
+    by = {r.rid: r for r in b.done}
+    assert by[1].status == -5
+    assert st.completed == 6 and st.extra["failed"] == 1
+    for r in b.done:
+        if r.status == 0:
+            T = 10.0 * r.Ny * r.Kn
+            assert 1e-3 * math.exp(-r.steps / T) < r.tol          # converged at its steps
+            assert 1e-3 * math.exp(-(r.steps - 100) / T) >= r.tol  # not a chunk earlier
