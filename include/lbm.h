@@ -179,8 +179,25 @@ int lbm_init(lbm_solver* s, const double* rho_host);
 int lbm_init_device(lbm_solver* s, const double* rho_device);
 
 /* Advance nsteps >= 0 time steps (Eq. nm.8 + streaming + walls), one fused
- * kernel launch per step on the solver's stream.  Asynchronous. */
+ * kernel launch per step on the solver's stream, or, for a resident channel
+ * (lbm_set_resident), up to 4096 steps per launch.  Asynchronous. */
 int lbm_step(lbm_solver* s, long nsteps);
+
+/* Resident chunks for tiny fp64 channels (no counterpart in the paper, which
+ * does not discuss execution).  A channel whose fp64 step runs on several
+ * lanes per node (at most 152*32*8 node-lanes) and whose rows fit one
+ * thread-block cluster (at most 16 CTAs of at most 8 warps, both lattices in
+ * their shared memory) runs many steps per launch, the cluster's barrier
+ * between steps, instead of one launch per step; lbm_step and
+ * lbm_run_to_steady then use it.  The result is bitwise that of the per-step
+ * launches.  enable: 1 (the default at lbm_create) or 0; anything else ->
+ * LBM_EINVAL.  Other precisions and larger channels ignore the setting. */
+int lbm_set_resident(lbm_solver* s, int enable);
+
+/* *ctas = CTAs of the cluster that runs this solver's resident chunks, 0 when
+ * it steps by single launches (not eligible, not placeable on this device, or
+ * disabled).  NULL pointer -> LBM_EINVAL. */
+int lbm_resident_ctas(lbm_solver* s, int* ctas);
 
 /* Step until max over nodes of |u_x(t) - u_x(t - dt)| < tol, tested every
  * check_every (>= 2) steps, or until max_steps in total.  Returns LBM_OK when

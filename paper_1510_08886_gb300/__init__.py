@@ -248,6 +248,17 @@ class Solver:
         check(_lib.lib().lbm_step(self._h, int(n)), "lbm_step")
         return self
 
+    def set_resident(self, enable):
+        """Resident cluster chunks for a tiny fp64 channel on (default) or off."""
+        check(_lib.lib().lbm_set_resident(self._h, 1 if enable else 0), "lbm_set_resident")
+        return self
+
+    def resident_ctas(self):
+        """CTAs of the cluster running this solve's resident chunks (0: per-step launches)."""
+        n = ctypes.c_int(0)
+        check(_lib.lib().lbm_resident_ctas(self._h, ctypes.byref(n)), "lbm_resident_ctas")
+        return n.value
+
     def run_to_steady(self, tol, max_steps, check_every=100):
         """Returns (converged, steps_done, last_du)."""
         steps = ctypes.c_long(0)

@@ -31,6 +31,9 @@ struct lbm_solver : lbm::SolveSpec {
     // run_to_steady chunks captured as CUDA graphs, one per starting lattice
     cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
     long chunk_K[2] = {0, 0};
+    // tiny fp64 channels: chunks of steps resident on one thread-block cluster
+    lbm::ClusterPlan cl{};
+    bool resident = true;
 };
 
 namespace lbm {
@@ -219,6 +222,14 @@ void fill_params_impl(const lbm::SolveSpec* s, KParams<C>& k) {
     k.two_tau = C(2 * s->tau);
     k.inv_2tau_dt = C(1.0 / (2 * s->tau + s->dt));
     k.half_tau = C(0.5 * s->tau);
+    k.hdt_gx = k.hdt * k.gx;
+    k.hdt_gy = k.hdt * k.gy;
+    k.tgx = k.two_tau * k.gx;
+    k.tgy = k.two_tau * k.gy;
+    k.ttc2 = k.two_tau * k.c2;
+    k.htc2 = k.half_tau * k.c2;
+    k.tc = k.tau * k.c;
+    k.cg = k.c * k.gx;
 }
 
 int cuda_status(cudaError_t e) {
@@ -465,18 +476,46 @@ int refresh_scale(lbm_solver* s) {
     return LBM_OK;
 }
 
+bool resident_on(const lbm_solver* s) {
+    return s->resident && s->cl.ctas > 0 && s->precision == LBM_FP64;
+}
+
+// K >= 1 steps on the resident cluster kernel, at most kClusterMaxK per launch;
+// the last step writes the moments, and with emit_prev the step before it
+// writes u_x to prev_ux (the final launch keeps >= 2 steps for that).
+int resident_steps(lbm_solver* s, long K, bool emit_prev) {
+    while (K > 0) {
+        const long n = K <= lbm::kClusterMaxK ? K : std::min(lbm::kClusterMaxK, K - 2);
+        const int next = int((s->cur + n) & 1);
+        const cudaError_t e = lbm::launch_chunk_cluster_fp64(
+            s->k64, s->cl, s->b.f[s->cur], s->b.f[next], s->b, int(n), emit_prev && n == K,
+            s->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        s->cur = next;
+        s->steps += n;
+        K -= n;
+    }
+    return LBM_OK;
+}
+
 // Enqueue one convergence chunk: K-1 steps (the last emitting moments), the
 // copy u_x -> prev, one more step, and the fp64 reductions into b.results.
+// Resident channels do the K steps in one launch that writes prev itself.
 int enqueue_chunk(lbm_solver* s, long K) {
-    for (long i = 0; i < K - 1; ++i) {
-        const int rc = launch_step(s, i == K - 2);
+    if (resident_on(s) && K >= 2) {
+        const int rc = resident_steps(s, K, true);
+        if (rc) return rc;
+    } else {
+        for (long i = 0; i < K - 1; ++i) {
+            const int rc = launch_step(s, i == K - 2);
+            if (rc) return rc;
+        }
+        cudaError_t e = cudaMemcpyAsync(s->b.prev_ux, s->b.ux, size_t(s->Nx) * s->Ny * 8,
+                                        cudaMemcpyDeviceToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        const int rc = launch_step(s, true);
         if (rc) return rc;
     }
-    cudaError_t e = cudaMemcpyAsync(s->b.prev_ux, s->b.ux, size_t(s->Nx) * s->Ny * 8,
-                                    cudaMemcpyDeviceToDevice, s->stream);
-    if (e != cudaSuccess) return cuda_status(e);
-    int rc = launch_step(s, true);
-    if (rc) return rc;
     const int n = s->Nx * s->Ny;
     k_reduce_partial<<<lbm::kReduceBlocks, lbm::kReduceThreads, 0, s->stream>>>(
         s->b.ux, s->b.prev_ux, n, s->b.partial);
@@ -554,6 +593,10 @@ int create_common(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, doub
     s->b.status = reinterpret_cast<unsigned*>(base + L.status);
     lbm::fill_params(*s, s->k64);
     lbm::fill_params(*s, s->k32);
+    if (precision == LBM_FP64) {
+        const int LP = lbm::warp_path_lanes(s->P, (long long)Nx * Ny);
+        if (LP) lbm::plan_cluster_fp64(s->k64, s->N, LP, s->cl);
+    }
     *out = s;
     return LBM_OK;
 }
@@ -672,6 +715,7 @@ int lbm_init_device(lbm_solver* s, const double* rho_device) {
 
 int lbm_step(lbm_solver* s, long nsteps) {
     if (!s || nsteps < 0) return LBM_EINVAL;
+    if (resident_on(s) && nsteps >= 2) return resident_steps(s, nsteps, false);
     for (long i = 0; i < nsteps; ++i) {
         const int rc = launch_step(s, i == nsteps - 1);
         if (rc) return rc;
@@ -696,12 +740,11 @@ int lbm_run_to_steady(lbm_solver* s, double tol, long max_steps, long check_ever
             if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
             if (e != cudaSuccess) { rc = cuda_status(e); break; }
         } else {
-            if (n > 1 && (rc = lbm_step(s, n - 1))) break;
-            cudaError_t e = cudaMemcpyAsync(s->b.prev_ux, s->b.ux, size_t(s->Nx) * s->Ny * 8,
-                                            cudaMemcpyDeviceToDevice, s->stream);
+            if ((rc = enqueue_chunk(s, n))) break;
+            cudaError_t e = cudaMemcpyAsync(r, s->b.results, 4 * sizeof(double),
+                                            cudaMemcpyDeviceToHost, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
             if (e != cudaSuccess) { rc = cuda_status(e); break; }
-            if ((rc = lbm_step(s, 1))) break;
-            if ((rc = reduce(s, true, r))) break;
         }
         du = r[1];
         if ((rc = read_status(s))) break;
@@ -712,6 +755,25 @@ int lbm_run_to_steady(lbm_solver* s, double tol, long max_steps, long check_ever
     if (steps_done) *steps_done = s->steps;
     if (last_du) *last_du = du;
     return rc;
+}
+
+int lbm_set_resident(lbm_solver* s, int enable) {
+    if (!s || (enable != 0 && enable != 1)) return LBM_EINVAL;
+    if (s->resident != bool(enable)) {
+        for (int i = 0; i < 2; ++i) {
+            if (s->chunk_exec[i]) cudaGraphExecDestroy(s->chunk_exec[i]);
+            s->chunk_exec[i] = nullptr;
+            s->chunk_K[i] = 0;
+        }
+    }
+    s->resident = bool(enable);
+    return LBM_OK;
+}
+
+int lbm_resident_ctas(lbm_solver* s, int* ctas) {
+    if (!s || !ctas) return LBM_EINVAL;
+    *ctas = resident_on(s) ? s->cl.ctas : 0;
+    return LBM_OK;
 }
 
 int lbm_moments(lbm_solver* s, double* rho, double* ux, double* uy) {

@@ -66,6 +66,9 @@ struct KParams {
     // scalars
     C c, c2, tau, dt, hdt, omega, one_m_omega, gx, gy;
     C two_tau, inv_2tau_dt, half_tau;
+    // products of constants (formed on the host in C, as the device would):
+    // hdt gx, hdt gy, two_tau gx, two_tau gy, two_tau c2, half_tau c2, tau c, c gx
+    C hdt_gx, hdt_gy, tgx, tgy, ttc2, htc2, tc, cg;
 };
 
 // Device buffers of one solver.
@@ -101,6 +104,32 @@ cudaError_t launch_absmax_fp16(const void* f, long long n, bool bf16, float* out
 // multiply every stored value by `factor` (a power of 2)
 cudaError_t launch_rescale_fp16(void* f, long long n, bool bf16, float factor,
                                 cudaStream_t st);
+
+// Tiny fp64 channels: lanes per node of the warp step (k_step_warp) for P pairs,
+// 0 when the channel is large enough for one node per thread (or P > 32).
+inline int warp_lanes(int P) { return P <= 8 ? 8 : (P <= 16 ? 16 : (P <= 32 ? 32 : 0)); }
+inline int warp_path_lanes(int P, long long ncell) {
+    const int LP = warp_lanes(P);
+    return (LP && ncell * LP <= 152ll * 32 * 8) ? LP : 0;
+}
+
+// Resident chunks of a tiny fp64 channel on one thread-block cluster
+// (k_cluster.cu): CTAs of at most kClusterThreads threads, shared memory padded
+// to kClusterSmemPad (more than half an SM's) so that no two share an SM.
+constexpr int kClusterThreads = 256;
+constexpr int kClusterSmemPad = 116 * 1024;
+constexpr long kClusterMaxK = 4096;           // steps per launch in lbm_step
+struct ClusterPlan {
+    int ctas = 0, rows = 0, threads = 0, N = 0, LP = 0;
+    int nb = 0, nt = 0;                       // terms of the bottom / top wall sums
+    size_t smem = 0;
+};
+// 1 and the plan if the channel can run resident, else 0 (pl.ctas = 0).
+int plan_cluster_fp64(const KParams<double>& k, int N, int LP, ClusterPlan& pl);
+// K steps from fin to fout (see k_chunk_cluster).
+cudaError_t launch_chunk_cluster_fp64(const KParams<double>& k, const ClusterPlan& pl,
+                                      const void* fin, void* fout, const DevBufs& b, int K,
+                                      bool emit_prev, cudaStream_t st);
 
 // Validated, canonicalised description of one channel solve (shared by the
 // single-solve API and the engine).

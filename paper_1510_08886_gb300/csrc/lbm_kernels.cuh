@@ -149,9 +149,9 @@ struct Acc4 {
 // column they land on, so the source column is x - e_x.  Terms in plane order,
 // nearest row first; fp64 accumulation (Acc4) in every precision; the fill
 // d_a = dPsi w_a is formed in the compute type.
-template <typename S, typename C>
-__device__ __noinline__ double wall_dpsi(const KParams<C>& k, const S* __restrict__ src, int x,
-                                         bool bottom) {
+template <typename S, typename C, class LD>
+__device__ __forceinline__ double wall_dpsi_by(const KParams<C>& k, int x, bool bottom,
+                                               const LD& ld) {
     Acc4 acc;
     int t = 0;
     for (int b = k.R; b < k.V; ++b) {
@@ -160,13 +160,21 @@ __device__ __noinline__ double wall_dpsi(const KParams<C>& k, const S* __restric
         int xs = x - k.sx[b];
         xs += (xs < 0) ? k.Nx : 0;
         const int n = bottom ? -ey : ey;
-        const S* pl = src + (long long)b * k.plane + xs;
         for (int j = 0; j < n; ++j) {
             const int row = bottom ? j : (k.Ny - 1 - j);
-            acc.add(t++, (double)ld_pop<S, C>(k, pl[(long long)row * k.Nx], b));
+            acc.add(t++, (double)ld_pop<S, C>(k, ld(b, row, xs), b));
         }
     }
     return acc.sum() * k.inv_den;
+}
+
+// The same sum read from a lattice in global memory ([V][Ny][Nx] planes).
+template <typename S, typename C>
+__device__ __noinline__ double wall_dpsi(const KParams<C>& k, const S* __restrict__ src, int x,
+                                         bool bottom) {
+    return wall_dpsi_by<S, C>(k, x, bottom, [&](int b, int row, int xs) {
+        return src[(long long)b * k.plane + (long long)row * k.Nx + xs];
+    });
 }
 
 // Number of wall terms of the planes before plane a of a compiled set.
@@ -239,8 +247,8 @@ __device__ __forceinline__ CellCoef<C> cell_coef(const KParams<C>& k, C drho, C 
     q.rho = C(1) + drho;
     const C inv = C(1) / q.rho;
     // Eq. nm.10: rho u = sum fbar xi + (dt/2) rho g
-    q.ux = fma(mul_rn(k.c, Jx), inv, mul_rn(k.hdt, k.gx));
-    q.uy = fma(mul_rn(k.c, Jy), inv, mul_rn(k.hdt, k.gy));
+    q.ux = fma(mul_rn(k.c, Jx), inv, k.hdt_gx);
+    q.uy = fma(mul_rn(k.c, Jy), inv, k.hdt_gy);
     q.utx = mul_rn(k.c, q.ux);
     q.uty = mul_rn(k.c, q.uy);
     const C u2 = fma(q.ux, q.ux, mul_rn(q.uy, q.uy));
@@ -264,18 +272,18 @@ __device__ __forceinline__ CellCoef<C> cell_coef(const KParams<C>& k, C drho, C 
         //   (2 tau + dt) A = -2 tau drho delta + 2 tau c^2 K
         //                    + dt rho (u u + tau (g u + u g))
         const C tdr = mul_rn(k.dt, q.rho);
-        const C tgx = mul_rn(k.two_tau, k.gx), tgy = mul_rn(k.two_tau, k.gy);
+        const C tgx = k.tgx, tgy = k.tgy;
         const C Axx = mul_rn(fma(k.two_tau, fma(k.c2, Kxx, -drho),
                                  mul_rn(tdr, fma(q.ux, q.ux, mul_rn(tgx, q.ux)))), k.inv_2tau_dt);
         const C Ayy = mul_rn(fma(k.two_tau, fma(k.c2, Kyy, -drho),
                                  mul_rn(tdr, fma(q.uy, q.uy, mul_rn(tgy, q.uy)))), k.inv_2tau_dt);
-        const C Axy = mul_rn(fma(mul_rn(k.two_tau, k.c2), Kxy,
+        const C Axy = mul_rn(fma(k.ttc2, Kxy,
                                  mul_rn(tdr, fma(q.ux, q.uy, mul_rn(k.tau, fma(k.gx, q.uy,
                                                                               mul_rn(k.gy, q.ux)))))),
                              k.inv_2tau_dt);
         if (N >= 3) {
             // third-order force term (1/2) A:((g.xi) H2(xi) - 2 g xi)
-            const C htc2 = mul_rn(k.half_tau, k.c2), tc = mul_rn(k.tau, k.c);
+            const C htc2 = k.htc2, tc = k.tc;
             q.qxx = mul_rn(htc2, Axx);
             q.qxy = mul_rn(htc2, Axy);   // multiplies 2 ex ey
             q.qyy = mul_rn(htc2, Ayy);
@@ -285,7 +293,7 @@ __device__ __forceinline__ CellCoef<C> cell_coef(const KParams<C>& k, C drho, C 
         } else {
             q.qxx = q.qxy = q.qyy = q.qtr = q.hx = q.hy = C(0);
         }
-        const C cg = mul_rn(k.c, k.gx);
+        const C cg = k.cg;
         q.trcg = mul_rn(q.tr, cg);
         q.k0 = mul_rn(cg, q.tr - q.qtr);
         q.cqxx = mul_rn(cg, q.qxx);
@@ -295,26 +303,43 @@ __device__ __forceinline__ CellCoef<C> cell_coef(const KParams<C>& k, C drho, C 
     return q;
 }
 
+// Constants of the +-e pair p (positive member e = (ex, ey)).
+template <typename C>
+struct PairConst {
+    C ex, ey, exx, exy2, eyy, ge, omw;
+};
+
+template <typename C>
+__device__ __forceinline__ PairConst<C> pair_const(const KParams<C>& k, int p) {
+    return PairConst<C>{k.pex[p], k.pey[p], k.pexx[p], k.pexy2[p], k.peyy[p], k.pge[p], k.pomw[p]};
+}
+
 // Relax one +-e pair (planes fp, fm) in place:
 //   d* = (1 - omega) d + omega w (feq/w - 1),  feq/w - 1 = Ge +- Go.
 template <bool FORCE, typename C>
-__device__ __forceinline__ void pair_update(const KParams<C>& k, const CellCoef<C>& q, int p,
-                                            C& fp, C& fm) {
-    const C ex = k.pex[p], ey = k.pey[p];
+__device__ __forceinline__ void pair_update_pc(const KParams<C>& k, const CellCoef<C>& q,
+                                               const PairConst<C>& pc, C& fp, C& fm) {
+    const C ex = pc.ex, ey = pc.ey;
     const C s = fma(q.uty, ey, q.utx * ex);
     const C t = mul_rn(s, s);
     C Ge = fma(t, fma(t, q.a2, q.a1), q.a0);
     C Go = mul_rn(s, fma(t, q.b1, q.b0));
     if (FORCE) {
-        const C ge = k.pge[p];
+        const C ge = pc.ge;
         // odd force part: tau rho (g.xi) + (tau/2)((g.xi) Q - 2 (g.A).xi)
-        const C halfQ = fma(q.qxx, k.pexx[p], fma(q.qxy, k.pexy2[p], fma(q.qyy, k.peyy[p], -q.qtr)));
+        const C halfQ = fma(q.qxx, pc.exx, fma(q.qxy, pc.exy2, fma(q.qyy, pc.eyy, -q.qtr)));
         Ge = fma(mul_rn(q.tr, ge), s, Ge);
         Go = fma(ge, q.tr + halfQ, Go) - fma(q.hx, ex, q.hy * ey);
     }
-    const C X = mul_rn(k.pomw[p], Ge);
-    fp = fma(k.one_m_omega, fp, fma(k.pomw[p], Go, X));
-    fm = fma(k.one_m_omega, fm, fma(-k.pomw[p], Go, X));
+    const C X = mul_rn(pc.omw, Ge);
+    fp = fma(k.one_m_omega, fp, fma(pc.omw, Go, X));
+    fm = fma(k.one_m_omega, fm, fma(-pc.omw, Go, X));
+}
+
+template <bool FORCE, typename C>
+__device__ __forceinline__ void pair_update(const KParams<C>& k, const CellCoef<C>& q, int p,
+                                            C& fp, C& fm) {
+    pair_update_pc<FORCE, C>(k, q, pair_const(k, p), fp, fm);
 }
 
 template <typename C>
@@ -323,13 +348,16 @@ __device__ __forceinline__ void flag_density(const CellCoef<C>& q, unsigned int*
 }
 
 template <typename C>
+__device__ __forceinline__ void store_moments(const CellCoef<C>& q, int cell, const DevBufs& b) {
+    b.rho[cell] = 1.0 + (double)q.drho;
+    b.ux[cell] = (double)q.ux;
+    b.uy[cell] = (double)q.uy;
+}
+
+template <typename C>
 __device__ __forceinline__ void emit_moments(const KParams<C>& k, const CellCoef<C>& q, int cell,
                                              const DevBufs& b) {
-    if (k.emit) {
-        b.rho[cell] = 1.0 + (double)q.drho;
-        b.ux[cell] = (double)q.ux;
-        b.uy[cell] = (double)q.uy;
-    }
+    if (k.emit) store_moments<C>(q, cell, b);
 }
 
 // Pull one population of plane a into node (x, y) of an interior row.
@@ -559,13 +587,45 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
     flag_density<C>(q, b.status);
 }
 
-// Step for tiny channels: LP lanes (a power of 2 >= P) cooperate on one node,
-// lane p holding the pair (R + p, R + P + p); the moments are summed over the
-// node's lanes by butterfly shuffles, every lane derives the node's
-// coefficients, and lane 0 also carries the rest population.  One warp per
-// block, so a channel of a few hundred nodes spreads over many SMs instead of
-// running on one (the fp64 step of a 64-node channel is otherwise bound by a
-// single SM's fp64 lanes).
+// One node of the tiny-channel step on LP lanes (a power of 2 >= P): lane p of
+// the node holds the pair (R + p, R + P + p) with constants pc and streamed (or
+// wall-filled) values fp, fm (0 on lanes p >= P), lane 0 also the rest value
+// f0 (0 without a rest velocity).  The moments are summed over the node's
+// lanes by butterfly shuffles and every lane derives the node's coefficients;
+// put(a, v) stores the post-collision population a.  The shuffles span the
+// warp: every lane of the warp calls this, `node` false on lanes without one.
+template <int LP, int N, typename C, class PUT>
+__device__ __forceinline__ CellCoef<C> warp_node(const KParams<C>& k, int p, bool node,
+                                                 const PairConst<C>& pc, C fp, C fm, C f0,
+                                                 const PUT& put) {
+    const bool act = node && p < k.P;
+    const C sum = fp + fm, dif = fp - fm;
+    C m[6] = {sum + f0, act ? mul_rn(pc.ex, dif) : C(0), act ? mul_rn(pc.ey, dif) : C(0),
+              act ? mul_rn(pc.exx, sum) : C(0), act ? mul_rn(pc.exy2, sum) : C(0),
+              act ? mul_rn(pc.eyy, sum) : C(0)};
+#pragma unroll
+    for (int o = LP / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) m[i] += __shfl_xor_sync(0xffffffffu, m[i], o);
+    CellCoef<C> q{};
+    if (!node) return q;
+    q = cell_coef<N, C>(k, m[0], m[1], m[2], m[3], C(0.5) * m[4], m[5]);
+    if (act) {
+        if (k.force)
+            pair_update_pc<true, C>(k, q, pc, fp, fm);
+        else
+            pair_update_pc<false, C>(k, q, pc, fp, fm);
+        put(k.R + p, fp);
+        put(k.R + k.P + p, fm);
+    }
+    if (p == 0 && k.R) put(0, fma(k.one_m_omega, f0, k.omw_rest * q.a0));
+    return q;
+}
+
+// Step for tiny channels: warp_node on every node, one warp per block, so a
+// channel of a few hundred nodes spreads over many SMs instead of running on
+// one (the fp64 step of a 64-node channel is otherwise bound by a single SM's
+// fp64 lanes).
 template <int LP, int N, typename S, typename C>
 __global__ void __launch_bounds__(32)
 k_step_warp(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __restrict__ dst,
@@ -575,7 +635,6 @@ k_step_warp(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* 
     const int cell = blockIdx.x * G + lane / LP;
     const int p = lane % LP;
     const bool node = cell < k.ncell;
-    const bool act = node && p < k.P;
     int y = 0, x = 0;
     if (node) {
         y = cell / k.Nx;
@@ -585,45 +644,23 @@ k_step_warp(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* 
     const C pt = (node && y >= k.Ny - k.maxey) ? C(wall_dpsi<S, C>(k, src, x, false)) : C(0);
     auto value = [&](int a) -> C {
         const int ys = y - k.ey[a];
-        if (ys < 0) return pb * k.cw[a];
-        if (ys >= k.Ny) return pt * k.cw[a];
+        if (ys < 0) return mul_rn(pb, k.cw[a]);
+        if (ys >= k.Ny) return mul_rn(pt, k.cw[a]);
         return pull<S, C>(k, src, a, x, y);
     };
-    C fp = C(0), fm = C(0), f0 = C(0);
-    if (act) {
-        fp = value(k.R + p);
-        fm = value(k.R + k.P + p);
-    }
-    if (node && p == 0 && k.R) f0 = value(0);
-    const C sum = fp + fm, dif = fp - fm;
-    const int pp = act ? p : 0;
-    C m[6] = {sum + f0, act ? mul_rn(k.pex[pp], dif) : C(0), act ? mul_rn(k.pey[pp], dif) : C(0),
-              act ? mul_rn(k.pexx[pp], sum) : C(0), act ? mul_rn(k.pexy2[pp], sum) : C(0),
-              act ? mul_rn(k.peyy[pp], sum) : C(0)};
-#pragma unroll
-    for (int o = LP / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int i = 0; i < 6; ++i) m[i] += __shfl_xor_sync(0xffffffffu, m[i], o);
-    if (!node) return;
-    const CellCoef<C> q = cell_coef<N, C>(k, m[0], m[1], m[2], m[3], C(0.5) * m[4], m[5]);
+    const bool act = node && p < k.P;
+    const PairConst<C> pc = pair_const(k, act ? p : 0);
+    const C fp = act ? value(k.R + p) : C(0);
+    const C fm = act ? value(k.R + k.P + p) : C(0);
+    const C f0 = (node && p == 0 && k.R) ? value(0) : C(0);
     unsigned rs = sr_seed<S, C>(k.seed, cell);
-    if (act) {
-        if (k.force)
-            pair_update<true, C>(k, q, p, fp, fm);
-        else
-            pair_update<false, C>(k, q, p, fp, fm);
-        dst[(long long)(k.R + p) * k.plane + cell] = st_pop<S, C>(k, fp, k.R + p, rs);
-        dst[(long long)(k.R + k.P + p) * k.plane + cell] = st_pop<S, C>(k, fm, k.R + k.P + p, rs);
-    }
-    if (p == 0) {
-        if (k.R) dst[cell] = st_pop<S, C>(k, fma(k.one_m_omega, f0, k.omw_rest * q.a0), 0, rs);
+    auto put = [&](int a, C v) { dst[(long long)a * k.plane + cell] = st_pop<S, C>(k, v, a, rs); };
+    const CellCoef<C> q = warp_node<LP, N, C>(k, p, node, pc, fp, fm, f0, put);
+    if (node && p == 0) {
         emit_moments<C>(k, q, cell, b);
         flag_density<C>(q, b.status);
     }
 }
-
-// lanes per node of the tiny-channel kernel for P pairs (0: not used, P > 32)
-inline int warp_lanes(int P) { return P <= 8 ? 8 : (P <= 16 ? 16 : (P <= 32 ? 32 : 0)); }
 
 template <int N, typename S, typename C>
 cudaError_t launch_warp(const KParams<C>& k, int LP, const S* src, S* dst, const DevBufs& b,
@@ -707,9 +744,8 @@ cudaError_t launch_step_n(const KParams<C>& k, const S* src, S* dst, const DevBu
     // fp64 channels too small to fill the GPU with one node per thread: several
     // lanes per node (k_step_warp) spread the fp64 work over more SMs
     if (sizeof(C) == 8) {
-        const int LP = warp_lanes(k.P);
-        if (LP && (long long)k.ncell * LP <= 152ll * 32 * 8)
-            return launch_warp<N, S, C>(k, LP, src, dst, b, st);
+        const int LP = warp_path_lanes(k.P, k.ncell);
+        if (LP) return launch_warp<N, S, C>(k, LP, src, dst, b, st);
     }
     switch (k.set_id) {
         case 0: k_step_ct<SetD2V16, N, S, C><<<g, kBlock, 0, st>>>(k, src, dst, b); break;
