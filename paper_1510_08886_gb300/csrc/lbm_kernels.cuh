@@ -177,6 +177,37 @@ __device__ __noinline__ double wall_dpsi(const KParams<C>& k, const S* __restric
     });
 }
 
+// The same sum spread over the first four lanes of a node (lane p of the node,
+// `lead` the node's first lane; every lane of the warp calls this): lane j < 4
+// of a node with `mine` set adds the terms j, j + 4, ... -- accumulator j of
+// Acc4 -- and two shuffles form (a0 + a1) + (a2 + a3) on the first lane, whose
+// result every lane of the node receives: the bits of wall_dpsi_by.
+template <typename S, typename C, class LD>
+__device__ __forceinline__ double wall_dpsi_lanes(const KParams<C>& k, int x, bool bottom,
+                                                  bool mine, int p, int lead, const LD& ld) {
+    constexpr unsigned FULL = 0xffffffffu;
+    double acc = 0.0;
+    if (mine && p < 4) {
+        int t = 0;
+        for (int b = k.R; b < k.V; ++b) {
+            const int ey = k.ey[b];
+            if (bottom ? (ey >= 0) : (ey <= 0)) continue;
+            int xs = x - k.sx[b];
+            xs += (xs < 0) ? k.Nx : 0;
+            const int n = bottom ? -ey : ey;
+            for (int j = 0; j < n; ++j, ++t) {
+                if ((t & 3) != p) continue;
+                const int row = bottom ? j : (k.Ny - 1 - j);
+                acc += (double)ld_pop<S, C>(k, ld(b, row, xs), b);
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    const double s2 = acc + __shfl_sync(FULL, acc, (lane + 1) & 31);
+    const double tot = s2 + __shfl_sync(FULL, s2, (lane + 2) & 31);
+    return __shfl_sync(FULL, tot * k.inv_den, lead);
+}
+
 // Number of wall terms of the planes before plane a of a compiled set.
 template <class SET, bool BOTTOM>
 __host__ __device__ constexpr int wall_terms_before(int a) {
@@ -342,9 +373,21 @@ __device__ __forceinline__ void pair_update(const KParams<C>& k, const CellCoef<
     pair_update_pc<FORCE, C>(k, q, pair_const(k, p), fp, fm);
 }
 
+// Flag a density that is not in (0, inf) (negative, zero, infinite or NaN).
+// Tested on the bit pattern: as a signed integer a positive finite non-zero
+// value lies strictly between 0 and the pattern of +inf; the integer compares
+// keep the test off the (slow) fp64 pipe.
 template <typename C>
 __device__ __forceinline__ void flag_density(const CellCoef<C>& q, unsigned int* status) {
-    if (!(q.rho > C(0) && q.rho < cinf<C>())) atomicOr(status, 1u);
+    bool ok;
+    if constexpr (sizeof(C) == 8) {
+        const long long bits = __double_as_longlong(q.rho);
+        ok = bits > 0 && bits < 0x7ff0000000000000ll;
+    } else {
+        const int bits = __float_as_int(q.rho);
+        ok = bits > 0 && bits < 0x7f800000;
+    }
+    if (!ok) atomicOr(status, 1u);
 }
 
 template <typename C>
@@ -587,6 +630,55 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
     flag_density<C>(q, b.status);
 }
 
+// Sum six per-lane values over the LP lanes of a node (LP = 8, 16, 32; lane p
+// of the node), leaving the six sums on every lane.  The summation tree is the
+// butterfly's -- partners p ^ LP/2, p ^ LP/4, ..., p ^ 1, each sum formed as
+// a + b of the two partners' values -- but the first three levels are a
+// reduce-scatter over eight slots (the six values and two zeros): at each
+// level a lane keeps half of its slots and adds the partner's copy of them, so
+// the level costs 4, 2, 1 additions instead of 6.  A lane then holds slot
+// (p / (LP/8)) mod 8; the last levels add that one value, and shuffles gather
+// the six sums.  IEEE addition is commutative, so every sum has the bits of the
+// six-wide butterfly.
+template <int LP, typename C>
+__device__ __forceinline__ void node_sum6(C (&m)[6], int p) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int B1 = LP / 2, B2 = LP / 4, B3 = LP / 8;
+    C v4[4];
+    {   // level 1: keep slots 0-3 (bit clear) or 4-7 (bit set), send the others
+        const bool hi = (p & B1) != 0;
+        const C s8[8] = {m[0], m[1], m[2], m[3], m[4], m[5], C(0), C(0)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const C keep = hi ? s8[4 + i] : s8[i];
+            const C send = hi ? s8[i] : s8[4 + i];
+            v4[i] = keep + __shfl_xor_sync(FULL, send, B1);
+        }
+    }
+    C v2[2];
+    {
+        const bool hi = (p & B2) != 0;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const C keep = hi ? v4[2 + i] : v4[i];
+            const C send = hi ? v4[i] : v4[2 + i];
+            v2[i] = keep + __shfl_xor_sync(FULL, send, B2);
+        }
+    }
+    C v;
+    {
+        const bool hi = (p & B3) != 0;
+        const C keep = hi ? v2[1] : v2[0];
+        const C send = hi ? v2[0] : v2[1];
+        v = keep + __shfl_xor_sync(FULL, send, B3);
+    }
+#pragma unroll
+    for (int o = B3 / 2; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    const int lead = (threadIdx.x & 31) - p;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) m[i] = __shfl_sync(FULL, v, lead + i * B3);
+}
+
 // One node of the tiny-channel step on LP lanes (a power of 2 >= P): lane p of
 // the node holds the pair (R + p, R + P + p) with constants pc and streamed (or
 // wall-filled) values fp, fm (0 on lanes p >= P), lane 0 also the rest value
@@ -603,10 +695,7 @@ __device__ __forceinline__ CellCoef<C> warp_node(const KParams<C>& k, int p, boo
     C m[6] = {sum + f0, act ? mul_rn(pc.ex, dif) : C(0), act ? mul_rn(pc.ey, dif) : C(0),
               act ? mul_rn(pc.exx, sum) : C(0), act ? mul_rn(pc.exy2, sum) : C(0),
               act ? mul_rn(pc.eyy, sum) : C(0)};
-#pragma unroll
-    for (int o = LP / 2; o > 0; o >>= 1)
-#pragma unroll
-        for (int i = 0; i < 6; ++i) m[i] += __shfl_xor_sync(0xffffffffu, m[i], o);
+    node_sum6<LP, C>(m, p);
     CellCoef<C> q{};
     if (!node) return q;
     q = cell_coef<N, C>(k, m[0], m[1], m[2], m[3], C(0.5) * m[4], m[5]);
@@ -640,8 +729,15 @@ k_step_warp(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* 
         y = cell / k.Nx;
         x = cell - y * k.Nx;
     }
-    const C pb = (node && y < k.maxey) ? C(wall_dpsi<S, C>(k, src, x, true)) : C(0);
-    const C pt = (node && y >= k.Ny - k.maxey) ? C(wall_dpsi<S, C>(k, src, x, false)) : C(0);
+    const bool wb = node && y < k.maxey, wt = node && y >= k.Ny - k.maxey;
+    auto ld = [&](int b, int row, int xs) {
+        return src[(long long)b * k.plane + (long long)row * k.Nx + xs];
+    };
+    const int lead = lane - p;
+    const C pb = __any_sync(0xffffffffu, wb) ? C(wall_dpsi_lanes<S, C>(k, x, true, wb, p, lead, ld))
+                                             : C(0);
+    const C pt = __any_sync(0xffffffffu, wt) ? C(wall_dpsi_lanes<S, C>(k, x, false, wt, p, lead, ld))
+                                             : C(0);
     auto value = [&](int a) -> C {
         const int ys = y - k.ey[a];
         if (ys < 0) return mul_rn(pb, k.cw[a]);
