@@ -273,25 +273,31 @@ def dvm_generator_section(lbm, with_oracle=True):
 def config1_section(lbm):
     """Config 1: D2V16, N=3, Nx=1 x Ny=64, Kn=0.1, Ma 1e-3, rho=1, run until
     max|du| < 1e-10 tested every 100 steps (<= 50k steps): wall time to steady
-    state on the GPU (fp64 and fp32; launched step by step on the default
-    stream, or as CUDA-graph chunks on a side stream) and with the fp64 CPU
-    oracle."""
+    state on the GPU and with the fp64 CPU oracle.  fp64: resident chunks on one
+    thread-block cluster (the default for so small a channel), on the default
+    stream and as CUDA-graph chunks on a side stream, and one launch per step
+    (resident off, graph chunks); fp32: one launch per step, default stream and
+    graph chunks."""
     import oracle
     Kn = 0.1
     g = lbm.force_for_mach(Kn)
     e, w, c = lbm.dvm("D2V16")
     out = {}
     side = torch_stream()
-    for prec, stream in (("fp64", None), ("fp32", None), ("fp64_graphs", side),
-                         ("fp32_graphs", side)):
-        s = lbm.Solver(e, w, c, 3, 1, 64, Kn, g, precision=prec.split("_")[0], stream=stream).init()
+    variants = (("fp64", "fp64", None, True), ("fp64_graphs", "fp64", side, True),
+                ("fp64_per_step_graphs", "fp64", side, False), ("fp32", "fp32", None, True),
+                ("fp32_graphs", "fp32", side, True))
+    for label, prec, stream, resident in variants:
+        s = lbm.Solver(e, w, c, 3, 1, 64, Kn, g, precision=prec, stream=stream)
+        s.set_resident(resident).init()
         s.run_to_steady(1e-10, 2000)            # warm-up (first launches, clocks)
         s.init()
         t0 = time.perf_counter()
         conv, steps, du = s.run_to_steady(1e-10, 50000)
         dt = time.perf_counter() - t0
-        out[prec] = {"converged": conv, "steps": steps, "seconds": dt, "steps_per_s": steps / dt,
-                     "mdot": s.mass_flow(), "us": s.slip_velocity()}
+        out[label] = {"converged": conv, "steps": steps, "seconds": dt, "steps_per_s": steps / dt,
+                      "resident_ctas": s.resident_ctas(), "mdot": s.mass_flow(),
+                      "us": s.slip_velocity()}
         s.close()
     ch = oracle.channel("D2V16", 3, 1, 64, Kn, g).init()
     t0 = time.perf_counter()
