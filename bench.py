@@ -34,7 +34,7 @@ import numpy as np  # noqa: E402
 METRIC = "GLUPS & %HBM roofline"
 # fp64 operations of one node update of the D2V33, N = 4 step counted by ncu
 # (2 DFMA + DMUL + DADD per node) on the compile-time-set kernel
-FP64_FLOPS_PER_NODE = 679
+FP64_FLOPS_PER_NODE = 672
 UNIT = "GLUPS"
 DVM, ORDER, NX, NY, SEED = "D2V33", 4, 4096, 512, 20151029
 WORKLOAD = ("channel D2V33 (S^{D2V33}_{Q9E132}), Hermite order 4, Nx=4096 periodic x "
