@@ -181,6 +181,8 @@ def batched_section(lbm, torch):
     work = batch_workload(256)
     sets = {n: lbm.dvm(n) for n in {it["dvm"] for it in work}}
     cells = sum(it["Nx"] * it["Ny"] for it in work)
+    # algorithmic bytes of one step: every node reads and writes its V fp32 populations
+    step_bytes = sum(2 * len(sets[it["dvm"]][1]) * 4 * it["Nx"] * it["Ny"] for it in work)
     need = sum(lbm.Engine.solve_bytes(*sets[it["dvm"]], it["Nx"], it["Ny"], "fp32") for it in work)
     eng = lbm.Engine("fp32", max_solves=256, arena_bytes=need + (64 << 20), chunk=100)
     for it in work:
@@ -217,7 +219,11 @@ def batched_section(lbm, torch):
     return {"workload": "256 channels, seed 20151030: Ny U{16..512}, Nx {1,64,256}, Kn log-U[0.01,1], "
                         "D2V33 N=4 / D3V107xz N=3, fp32",
             "cells": cells, "GLUPS_engine": batched, "GLUPS_per_solve_api": per_solve,
-            "speedup": batched / per_solve, "timed_steps": chunks * 100}
+            "speedup": batched / per_solve, "timed_steps": chunks * 100,
+            "bytes_per_step": step_bytes,
+            "achieved_GBs": step_bytes * batched * 1e9 / cells / 1e9,
+            "hbm_frac": step_bytes * batched / cells / measured_peaks()[0],
+            "hbm_peak_kind": measured_peaks()[1]}
 
 
 def torch_stream():

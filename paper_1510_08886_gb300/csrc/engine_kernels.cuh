@@ -33,9 +33,19 @@ struct EngineTile {
     int cell0;
 };
 
+// Registers per thread allowed beyond the populations' share (min_blocks_for),
+// chosen per set from ptxas's spill report: the tile loop's addresses and flags
+// need ~12; with the solve's constants read from shared memory the 53-velocity
+// set fits 96 registers (20 warps per SM), while the 48-velocity set still
+// spills there and keeps 24.
+template <class SET>
+constexpr int engine_extra_regs() {
+    return SET::R + 2 * SET::P == 53 ? 0 : (SET::P > 20 ? 24 : 12);
+}
+
 // emit: 0 = nothing, 1 = rho, u_x, u_y into the moment fields, 2 = u_x into prev
 template <class SET, int N, typename S, typename C>
-__global__ void __launch_bounds__(kBlock, min_blocks_for(SET::R + 2 * SET::P + (SET::P > 20 ? 24 : 12),
+__global__ void __launch_bounds__(kBlock, min_blocks_for(SET::R + 2 * SET::P + engine_extra_regs<SET>(),
                                                          sizeof(C)))
 k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __restrict__ tiles,
               const int* __restrict__ ntiles_p, const int* __restrict__ tile_off_p,
@@ -45,6 +55,7 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
     __shared__ const S* sp[V];
     __shared__ S* dp[V];
     __shared__ int s_first;
+    __shared__ KParams<C> s_k;
     const int ntiles = *ntiles_p;
     tiles += *tile_off_p;
     const unsigned seed = *seed_p + unsigned(parity);
@@ -59,9 +70,15 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
         for (int t = first; t < last; ++t) {
             const EngineTile tile = tiles[t];
             const EngineSolve<C>& B = solves[tile.slot];
-            const KParams<C>& k = B.k;
+            const KParams<C>& k = s_k;
             if (tile.slot != cur_slot) {
                 // per-plane pull bases (interior offset folded in) and store bases
+                __syncthreads();
+                {
+                    const int* srcw = reinterpret_cast<const int*>(&B.k);
+                    int* dstw = reinterpret_cast<int*>(&s_k);
+                    for (int i = threadIdx.x; i < int(sizeof(KParams<C>) / 4); i += kBlock) dstw[i] = srcw[i];
+                }
                 __syncthreads();
                 const int cur = B.phase ^ parity;
                 if (threadIdx.x < V) {
