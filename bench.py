@@ -455,9 +455,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed_run(precision, Kn, lb, steps, warmup, sample_clocks=False):
-        s = lbm.Solver(e, w, c, ORDER, NX, NY, Kn, lbm.force_for_mach(Kn), precision=precision,
-                       stream=stream)
+    def timed_run(precision, Kn, lb, steps, warmup, sample_clocks=False, force=True):
+        s = lbm.Solver(e, w, c, ORDER, NX, NY, Kn, lbm.force_for_mach(Kn) if force else 0.0,
+                       precision=precision, stream=stream)
         s.init(rho_dev)
         for _ in range(warmup):
             s.step(lb)
@@ -536,20 +536,23 @@ def main():
     e2e_value, _ = replicas.aggregate_rate(ncell * args.steps * args.lb_steps / 1e9,
                                            e2e_ms * 1e-3, dist, "cuda")
 
-    # ---- variants: both precisions, Kn in {0.01, 0.1, 1.0} -----------------
+    # ---- variants: both precisions, Kn in {0.01, 0.1, 1.0}; g = 0 ------------
     variants = []
     if not args.no_variants:
-        for prec, kns in (("fp64", (0.01, 0.1, 1.0)), ("fp32", (0.01, 0.1, 1.0)),
-                          ("fp16", (0.1,)), ("bf16", (0.1,))):
-            for Kn in kns:
-                lb = 200
-                vms, _, vst, vm = timed_run(prec, Kn, lb, 1, 1)
-                el = ELEM[prec]
-                variants.append({
-                    "precision": prec, "Kn": Kn, "lb_steps": lb,
-                    "GLUPS": ncell * lb / (vms * 1e-3) / 1e9,
-                    "achieved_GBs": 2 * V * el * ncell * lb / (vms * 1e-3) / 1e9,
-                    "mdot": vm, "status": vst})
+        runs = [(prec, Kn, True) for prec, kns in (("fp64", (0.01, 0.1, 1.0)),
+                                                   ("fp32", (0.01, 0.1, 1.0)),
+                                                   ("fp16", (0.1,)), ("bf16", (0.1,)))
+                for Kn in kns]
+        runs += [("fp64", 0.1, False), ("fp32", 0.1, False)]   # force-free specialisation
+        for prec, Kn, force in runs:
+            lb = 200
+            vms, _, vst, vm = timed_run(prec, Kn, lb, 1, 1, force=force)
+            el = ELEM[prec]
+            variants.append({
+                "precision": prec, "Kn": Kn, "g": "8 tau 1e-3" if force else 0.0, "lb_steps": lb,
+                "GLUPS": ncell * lb / (vms * 1e-3) / 1e9,
+                "achieved_GBs": 2 * V * el * ncell * lb / (vms * 1e-3) / 1e9,
+                "mdot": vm if force else None, "status": vst})
 
     batched = None if args.no_batched else batched_section(lbm, torch)
     serving = None if args.no_serving else serving_section(lbm, args.serve_seconds,
