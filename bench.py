@@ -282,8 +282,8 @@ def config1_section(lbm):
     state on the GPU and with the fp64 CPU oracle.  fp64: resident chunks on one
     thread-block cluster (the default for so small a channel), on the default
     stream and as CUDA-graph chunks on a side stream, and one launch per step
-    (resident off, graph chunks); fp32: one launch per step, default stream and
-    graph chunks."""
+    (resident off, graph chunks); fp32: resident chunks, default stream and graph
+    chunks."""
     import oracle
     Kn = 0.1
     g = lbm.force_for_mach(Kn)

@@ -183,15 +183,15 @@ int lbm_init_device(lbm_solver* s, const double* rho_device);
  * (lbm_set_resident), up to 4096 steps per launch.  Asynchronous. */
 int lbm_step(lbm_solver* s, long nsteps);
 
-/* Resident chunks for tiny fp64 channels (no counterpart in the paper, which
- * does not discuss execution).  A channel whose fp64 step runs on several
- * lanes per node (at most 152*32*8 node-lanes) and whose rows fit one
+/* Resident chunks for tiny fp64 and fp32 channels (no counterpart in the
+ * paper, which does not discuss execution).  A channel whose step runs on
+ * several lanes per node (at most 152*32*8 node-lanes) and whose rows fit one
  * thread-block cluster (at most 16 CTAs of at most 8 warps, both lattices in
  * their shared memory) runs many steps per launch, the cluster's barrier
  * between steps, instead of one launch per step; lbm_step and
  * lbm_run_to_steady then use it.  The result is bitwise that of the per-step
  * launches.  enable: 1 (the default at lbm_create) or 0; anything else ->
- * LBM_EINVAL.  Other precisions and larger channels ignore the setting. */
+ * LBM_EINVAL.  16-bit storage and larger channels ignore the setting. */
 int lbm_set_resident(lbm_solver* s, int enable);
 
 /* *ctas = CTAs of the cluster that runs this solver's resident chunks, 0 when

@@ -249,7 +249,7 @@ class Solver:
         return self
 
     def set_resident(self, enable):
-        """Resident cluster chunks for a tiny fp64 channel on (default) or off."""
+        """Resident cluster chunks for a tiny fp64 / fp32 channel on (default) or off."""
         check(_lib.lib().lbm_set_resident(self._h, 1 if enable else 0), "lbm_set_resident")
         return self
 

@@ -1,4 +1,4 @@
-// Resident chunk of a tiny fp64 channel on one thread-block cluster.
+// Resident chunk of a tiny fp64 or fp32 channel on one thread-block cluster.
 //
 // A channel of a few hundred nodes cannot fill the GPU, so its per-step cost is
 // launch latency plus one node's dependency chain.  This kernel runs K steps
@@ -182,22 +182,23 @@ k_chunk_cluster(const __grid_constant__ KParams<C> k, const S* fin, S* fout, con
     }
 }
 
-template <int LP, int N>
+template <int LP, int N, typename C>
 void* cluster_kernel() {
-    return reinterpret_cast<void*>(&k_chunk_cluster<LP, N, double, double>);
+    return reinterpret_cast<void*>(&k_chunk_cluster<LP, N, C, C>);
 }
 
+template <typename C>
 void* pick_kernel(int N, int LP) {
     switch (LP * 10 + N) {
-        case 82: return cluster_kernel<8, 2>();
-        case 83: return cluster_kernel<8, 3>();
-        case 84: return cluster_kernel<8, 4>();
-        case 162: return cluster_kernel<16, 2>();
-        case 163: return cluster_kernel<16, 3>();
-        case 164: return cluster_kernel<16, 4>();
-        case 322: return cluster_kernel<32, 2>();
-        case 323: return cluster_kernel<32, 3>();
-        case 324: return cluster_kernel<32, 4>();
+        case 82: return cluster_kernel<8, 2, C>();
+        case 83: return cluster_kernel<8, 3, C>();
+        case 84: return cluster_kernel<8, 4, C>();
+        case 162: return cluster_kernel<16, 2, C>();
+        case 163: return cluster_kernel<16, 3, C>();
+        case 164: return cluster_kernel<16, 4, C>();
+        case 322: return cluster_kernel<32, 2, C>();
+        case 323: return cluster_kernel<32, 3, C>();
+        case 324: return cluster_kernel<32, 4, C>();
         default: return nullptr;
     }
 }
@@ -219,13 +220,15 @@ cudaLaunchConfig_t cluster_config(const ClusterPlan& pl, cudaStream_t st, cudaLa
 
 }  // namespace
 
-// Choose the cluster for an fp64 channel whose step runs on LP lanes per node:
+// Choose the cluster for a channel (fp64 or fp32 storage and arithmetic, C)
+// whose step runs on LP lanes per node:
 // the rows split evenly over at most 16 CTAs (8 where 16 cannot be placed), at
 // most kClusterThreads / 32 warps per CTA, shared memory padded so that each CTA
 // has an SM (and its fp64 lanes) of its own.  pl.ctas = 0: not resident.
-int plan_cluster_fp64(const KParams<double>& k, int N, int LP, ClusterPlan& pl) {
+template <typename C>
+int plan_cluster_t(const KParams<C>& k, int N, int LP, ClusterPlan& pl) {
     pl = ClusterPlan{};
-    void* fn = pick_kernel(N, LP);
+    void* fn = pick_kernel<C>(N, LP);
     if (!fn) return 0;
     int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -244,8 +247,8 @@ int plan_cluster_fp64(const KParams<double>& k, int N, int LP, ClusterPlan& pl) 
         const int ctas = (k.Ny + rows - 1) / rows;
         const int groups = (rows * k.Nx + G - 1) / G;      // warps of work per CTA
         if (groups > kClusterThreads / 32) continue;
-        const size_t need = ((size_t(2) * k.V * rows * k.Nx * sizeof(double) + 15) & ~size_t(15)) +
-                            size_t(nb + nt) * sizeof(WallTerm<double>);
+        const size_t need = ((size_t(2) * k.V * rows * k.Nx * sizeof(C) + 15) & ~size_t(15)) +
+                            size_t(nb + nt) * sizeof(WallTerm<C>);
         const size_t smem = std::max(need, size_t(kClusterSmemPad));
         if (smem > size_t(optin)) continue;
         ClusterPlan c;
@@ -278,19 +281,37 @@ int plan_cluster_fp64(const KParams<double>& k, int N, int LP, ClusterPlan& pl) 
     return 0;
 }
 
-cudaError_t launch_chunk_cluster_fp64(const KParams<double>& k, const ClusterPlan& pl,
-                                      const void* fin, void* fout, const DevBufs& b, int K,
-                                      bool emit_prev, cudaStream_t st) {
-    void* fn = pick_kernel(pl.N, pl.LP);
+template <typename C>
+cudaError_t launch_chunk_cluster_t(const KParams<C>& k, const ClusterPlan& pl, const void* fin,
+                                   void* fout, const DevBufs& b, int K, bool emit_prev,
+                                   cudaStream_t st) {
+    void* fn = pick_kernel<C>(pl.N, pl.LP);
     if (!fn || pl.ctas < 1 || K < 1) return cudaErrorInvalidValue;
     cudaLaunchAttribute at[1];
     const cudaLaunchConfig_t cfg = cluster_config(pl, st, at);
-    const double* src = static_cast<const double*>(fin);
-    double* dst = static_cast<double*>(fout);
+    const C* src = static_cast<const C*>(fin);
+    C* dst = static_cast<C*>(fout);
     int rows = pl.rows, ep = emit_prev ? 1 : 0, nb = pl.nb, nt = pl.nt;
-    void* args[] = {const_cast<KParams<double>*>(&k), &src, &dst, const_cast<DevBufs*>(&b),
+    void* args[] = {const_cast<KParams<C>*>(&k), &src, &dst, const_cast<DevBufs*>(&b),
                     &K, &rows, &ep, &nb, &nt};
     return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+int plan_cluster(const KParams<double>& k, int N, int LP, ClusterPlan& pl) {
+    return plan_cluster_t(k, N, LP, pl);
+}
+int plan_cluster(const KParams<float>& k, int N, int LP, ClusterPlan& pl) {
+    return plan_cluster_t(k, N, LP, pl);
+}
+cudaError_t launch_chunk_cluster(const KParams<double>& k, const ClusterPlan& pl, const void* fin,
+                                 void* fout, const DevBufs& b, int K, bool emit_prev,
+                                 cudaStream_t st) {
+    return launch_chunk_cluster_t(k, pl, fin, fout, b, K, emit_prev, st);
+}
+cudaError_t launch_chunk_cluster(const KParams<float>& k, const ClusterPlan& pl, const void* fin,
+                                 void* fout, const DevBufs& b, int K, bool emit_prev,
+                                 cudaStream_t st) {
+    return launch_chunk_cluster_t(k, pl, fin, fout, b, K, emit_prev, st);
 }
 
 }  // namespace lbm

@@ -31,7 +31,7 @@ struct lbm_solver : lbm::SolveSpec {
     // run_to_steady chunks captured as CUDA graphs, one per starting lattice
     cudaGraphExec_t chunk_exec[2] = {nullptr, nullptr};
     long chunk_K[2] = {0, 0};
-    // tiny fp64 channels: chunks of steps resident on one thread-block cluster
+    // tiny fp64 / fp32 channels: chunks of steps resident on one thread-block cluster
     lbm::ClusterPlan cl{};
     bool resident = true;
 };
@@ -477,7 +477,8 @@ int refresh_scale(lbm_solver* s) {
 }
 
 bool resident_on(const lbm_solver* s) {
-    return s->resident && s->cl.ctas > 0 && s->precision == LBM_FP64;
+    return s->resident && s->cl.ctas > 0 &&
+           (s->precision == LBM_FP64 || s->precision == LBM_FP32);
 }
 
 // K >= 1 steps on the resident cluster kernel, at most kClusterMaxK per launch;
@@ -487,9 +488,13 @@ int resident_steps(lbm_solver* s, long K, bool emit_prev) {
     while (K > 0) {
         const long n = K <= lbm::kClusterMaxK ? K : std::min(lbm::kClusterMaxK, K - 2);
         const int next = int((s->cur + n) & 1);
-        const cudaError_t e = lbm::launch_chunk_cluster_fp64(
-            s->k64, s->cl, s->b.f[s->cur], s->b.f[next], s->b, int(n), emit_prev && n == K,
-            s->stream);
+        const bool prev = emit_prev && n == K;
+        const cudaError_t e =
+            s->precision == LBM_FP64
+                ? lbm::launch_chunk_cluster(s->k64, s->cl, s->b.f[s->cur], s->b.f[next], s->b,
+                                            int(n), prev, s->stream)
+                : lbm::launch_chunk_cluster(s->k32, s->cl, s->b.f[s->cur], s->b.f[next], s->b,
+                                            int(n), prev, s->stream);
         if (e != cudaSuccess) return cuda_status(e);
         s->cur = next;
         s->steps += n;
@@ -593,9 +598,10 @@ int create_common(const lbm_dvm* dvm, int order, int Nx, int Ny, double Kn, doub
     s->b.status = reinterpret_cast<unsigned*>(base + L.status);
     lbm::fill_params(*s, s->k64);
     lbm::fill_params(*s, s->k32);
-    if (precision == LBM_FP64) {
+    if (precision == LBM_FP64 || precision == LBM_FP32) {
         const int LP = lbm::warp_path_lanes(s->P, (long long)Nx * Ny);
-        if (LP) lbm::plan_cluster_fp64(s->k64, s->N, LP, s->cl);
+        if (LP && precision == LBM_FP64) lbm::plan_cluster(s->k64, s->N, LP, s->cl);
+        if (LP && precision == LBM_FP32) lbm::plan_cluster(s->k32, s->N, LP, s->cl);
     }
     *out = s;
     return LBM_OK;

@@ -105,7 +105,7 @@ cudaError_t launch_absmax_fp16(const void* f, long long n, bool bf16, float* out
 cudaError_t launch_rescale_fp16(void* f, long long n, bool bf16, float factor,
                                 cudaStream_t st);
 
-// Tiny fp64 channels: lanes per node of the warp step (k_step_warp) for P pairs,
+// Tiny fp64 / fp32 channels: lanes per node of the warp step (k_step_warp) for P pairs,
 // 0 when the channel is large enough for one node per thread (or P > 32).
 inline int warp_lanes(int P) { return P <= 8 ? 8 : (P <= 16 ? 16 : (P <= 32 ? 32 : 0)); }
 inline int warp_path_lanes(int P, long long ncell) {
@@ -113,7 +113,7 @@ inline int warp_path_lanes(int P, long long ncell) {
     return (LP && ncell * LP <= 152ll * 32 * 8) ? LP : 0;
 }
 
-// Resident chunks of a tiny fp64 channel on one thread-block cluster
+// Resident chunks of a tiny fp64 or fp32 channel on one thread-block cluster
 // (k_cluster.cu): CTAs of at most kClusterThreads threads, shared memory padded
 // to kClusterSmemPad (more than half an SM's) so that no two share an SM.
 constexpr int kClusterThreads = 256;
@@ -125,11 +125,15 @@ struct ClusterPlan {
     size_t smem = 0;
 };
 // 1 and the plan if the channel can run resident, else 0 (pl.ctas = 0).
-int plan_cluster_fp64(const KParams<double>& k, int N, int LP, ClusterPlan& pl);
+int plan_cluster(const KParams<double>& k, int N, int LP, ClusterPlan& pl);
+int plan_cluster(const KParams<float>& k, int N, int LP, ClusterPlan& pl);
 // K steps from fin to fout (see k_chunk_cluster).
-cudaError_t launch_chunk_cluster_fp64(const KParams<double>& k, const ClusterPlan& pl,
-                                      const void* fin, void* fout, const DevBufs& b, int K,
-                                      bool emit_prev, cudaStream_t st);
+cudaError_t launch_chunk_cluster(const KParams<double>& k, const ClusterPlan& pl, const void* fin,
+                                 void* fout, const DevBufs& b, int K, bool emit_prev,
+                                 cudaStream_t st);
+cudaError_t launch_chunk_cluster(const KParams<float>& k, const ClusterPlan& pl, const void* fin,
+                                 void* fout, const DevBufs& b, int K, bool emit_prev,
+                                 cudaStream_t st);
 
 // Validated, canonicalised description of one channel solve (shared by the
 // single-solve API and the engine).

@@ -837,9 +837,10 @@ template <int N, typename S, typename C>
 cudaError_t launch_step_n(const KParams<C>& k, const S* src, S* dst, const DevBufs& b,
                           cudaStream_t st) {
     const dim3 g = grid_for(k);
-    // fp64 channels too small to fill the GPU with one node per thread: several
-    // lanes per node (k_step_warp) spread the fp64 work over more SMs
-    if (sizeof(C) == 8) {
+    // fp64 and fp32 channels too small to fill the GPU with one node per
+    // thread: several lanes per node (k_step_warp) spread the work over more
+    // SMs, and the same body runs resident chunks on a cluster (k_cluster.cu)
+    if (sizeof(C) == 8 || sizeof(S) == 4) {
         const int LP = warp_path_lanes(k.P, k.ncell);
         if (LP) return launch_warp<N, S, C>(k, LP, src, dst, b, st);
     }

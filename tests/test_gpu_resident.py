@@ -1,4 +1,4 @@
-"""Resident chunks of tiny fp64 channels (one thread-block cluster, both
+"""Resident chunks of tiny fp64 and fp32 channels (one thread-block cluster, both
 lattices in distributed shared memory, many steps per launch) against the
 per-step launches of the same step: bitwise equal states, moments and
 convergence decisions; and against the fp64 oracle."""
@@ -18,12 +18,12 @@ def _built():
     __graft_entry__.build_library()
 
 
-def _solver(name, N, Nx, Ny, Kn, resident, stream=None, rho=None):
+def _solver(name, N, Nx, Ny, Kn, resident, stream=None, rho=None, precision="fp64"):
     import paper_1510_08886_gb300 as lbm
     e, w, c = lbm.dvm(name)
     g = oracle.force_for_mach(Kn, 1e-2)
-    s = lbm.Solver(e, w, c, N, Nx, Ny, Kn, g, stream=stream).set_resident(resident)
-    return s.init(rho)
+    s = lbm.Solver(e, w, c, N, Nx, Ny, Kn, g, stream=stream, precision=precision)
+    return s.set_resident(resident).init(rho)
 
 
 # config 1; Nx > 1 with a ragged last CTA; rows per CTA < max|e_y| (the wall
@@ -33,11 +33,12 @@ SHAPES = [("D2V16", 3, 1, 64), ("D2V16", 3, 5, 37), ("D2V33", 4, 3, 20), ("D2V33
           ("D2V16", 3, 2, 4), ("D3V107xz", 3, 1, 48), ("D2V32", 3, 2, 21), ("D2V16", 2, 1, 16)]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("name,N,Nx,Ny", SHAPES)
-def test_resident_steps_bitwise_equal_launched(name, N, Nx, Ny):
+def test_resident_steps_bitwise_equal_launched(name, N, Nx, Ny, precision):
     rho = rho_field(Nx, Ny, seed=5, amplitude=1e-3)
-    a = _solver(name, N, Nx, Ny, 0.2, True, rho=rho)
-    b = _solver(name, N, Nx, Ny, 0.2, False, rho=rho)
+    a = _solver(name, N, Nx, Ny, 0.2, True, rho=rho, precision=precision)
+    b = _solver(name, N, Nx, Ny, 0.2, False, rho=rho, precision=precision)
     assert a.resident_ctas() > 0 and b.resident_ctas() == 0
     for n in (1, 2, 123):
         a.step(n)
@@ -47,10 +48,11 @@ def test_resident_steps_bitwise_equal_launched(name, N, Nx, Ny):
             assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("name,N,Nx,Ny", SHAPES[:4])
-def test_resident_run_to_steady_bitwise(name, N, Nx, Ny):
-    a = _solver(name, N, Nx, Ny, 0.1, True)
-    b = _solver(name, N, Nx, Ny, 0.1, False)
+def test_resident_run_to_steady_bitwise(name, N, Nx, Ny, precision):
+    a = _solver(name, N, Nx, Ny, 0.1, True, precision=precision)
+    b = _solver(name, N, Nx, Ny, 0.1, False, precision=precision)
     ra = a.run_to_steady(1e-9, 20000, check_every=50)
     rb = b.run_to_steady(1e-9, 20000, check_every=50)
     assert ra == rb
@@ -107,12 +109,28 @@ def test_resident_checkpoint_into_launched_solver():
     assert np.array_equal(a.populations(), b.populations())
 
 
+def test_config1_fp32_resident_matches_oracle():
+    """Config 1 in fp32 on the resident path: mass flow and slip velocity at
+    steady state within the fp32 tolerance (1e-4) of the fp64 oracle."""
+    import paper_1510_08886_gb300 as lbm
+    Kn = 0.1
+    g = oracle.force_for_mach(Kn)
+    e, w, c = lbm.dvm("D2V16")
+    s = lbm.Solver(e, w, c, 3, 1, 64, Kn, g, precision="fp32").init()
+    assert s.resident_ctas() > 0
+    ref = oracle.channel("D2V16", 3, 1, 64, Kn, g).init()
+    assert s.run_to_steady(1e-10, 50000)[0] and ref.run_to_steady(1e-10, 50000)[0]
+    assert abs(s.mass_flow() / ref.mass_flow() - 1) < 1e-4
+    assert abs(s.slip_velocity() / ref.slip_velocity() - 1) < 1e-4
+
+
 def test_resident_eligibility():
-    """Only fp64 channels small enough for one cluster run resident."""
+    """Only fp64 and fp32 channels small enough for one cluster run resident."""
     import paper_1510_08886_gb300 as lbm
     e, w, c = lbm.dvm("D2V16")
     assert lbm.Solver(e, w, c, 3, 64, 512, 0.1, 1e-3).resident_ctas() == 0
-    assert lbm.Solver(e, w, c, 3, 1, 64, 0.1, 1e-3, precision="fp32").resident_ctas() == 0
+    assert lbm.Solver(e, w, c, 3, 1, 64, 0.1, 1e-3, precision="fp32").resident_ctas() > 0
+    assert lbm.Solver(e, w, c, 3, 1, 64, 0.1, 1e-3, precision="fp16").resident_ctas() == 0
     s = lbm.Solver(e, w, c, 3, 1, 64, 0.1, 1e-3)
     assert 1 <= s.resident_ctas() <= 16
     assert s.set_resident(False).resident_ctas() == 0
