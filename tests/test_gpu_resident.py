@@ -66,6 +66,22 @@ def test_resident_run_to_steady_bitwise(name, N, Nx, Ny, precision):
     assert np.array_equal(a.populations(), b.populations())
 
 
+@pytest.mark.parametrize("check_every", [2, 3])
+def test_resident_smallest_chunks(check_every):
+    """Chunks of 2 and 3 steps: the step that writes u_x for the convergence
+    test is the chunk's first (or second) step; tests and steps agree with the
+    per-step launches bit for bit, on the default stream and in graphs."""
+    for stream in (None, torch.cuda.Stream()):
+        a = _solver("D2V16", 3, 1, 64, 0.1, True, stream=stream)
+        b = _solver("D2V16", 3, 1, 64, 0.1, False, stream=stream)
+        ra = a.run_to_steady(1e-16, 41, check_every=check_every)
+        rb = b.run_to_steady(1e-16, 41, check_every=check_every)
+        assert ra == rb and ra[1] == 41
+        assert np.array_equal(a.populations(), b.populations())
+        for x, y in zip(a.moments(), b.moments()):
+            assert np.array_equal(x, y)
+
+
 def test_resident_graph_chunks_and_long_launch_split():
     """Graph-captured resident chunks on a side stream, and an lbm_step longer
     than one resident launch (4096 steps), equal the per-step launches."""
