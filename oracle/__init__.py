@@ -54,7 +54,7 @@ class _Params(ctypes.Structure):
                 ("w", ctypes.POINTER(ctypes.c_double)),
                 ("c", ctypes.c_double), ("tau", ctypes.c_double),
                 ("dt", ctypes.c_double), ("gx", ctypes.c_double),
-                ("gy", ctypes.c_double)]
+                ("gy", ctypes.c_double), ("wall_mode", ctypes.c_int)]
 
 
 def _dp(a):
@@ -80,7 +80,7 @@ class Channel:
     c: lattice speed; N: Hermite order; g: body acceleration along x.
     """
 
-    def __init__(self, e, w, c, N, Nx, Ny, Kn, g, gy=0.0):
+    def __init__(self, e, w, c, N, Nx, Ny, Kn, g, gy=0.0, wall="plain"):
         e = np.asarray(e)
         self.V = len(e)
         self.Nx, self.Ny, self.N = int(Nx), int(Ny), int(N)
@@ -93,7 +93,8 @@ class Channel:
         self.p = _Params(self.V, self.Nx, self.Ny, self.N,
                          self.ex.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                          self.ey.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                         _dp(self.w), self.c, self.tau, self.dt, self.g, float(gy))
+                         _dp(self.w), self.c, self.tau, self.dt, self.g, float(gy),
+                         {"plain": 0, "transformed": 1}[wall])
         self.f = np.zeros((self.V, self.Ny, self.Nx))
         self.work = np.zeros_like(self.f)
         self.steps = 0
@@ -215,10 +216,11 @@ class Channel:
         return out
 
 
-def channel(name, N, Nx, Ny, Kn, g, tables=None):
+def channel(name, N, Nx, Ny, Kn, g, tables=None, wall="plain"):
     """Channel for a named DVM (a 2D table, or '<3D name>xz' for the (x, z)
-    marginal of a 3D table)."""
+    marginal of a 3D table).  wall: "plain" (the unknown fbar is Psi rho_w w_a)
+    or "transformed" (the condition holds for f, fbar through Eq. nm.7)."""
     if tables is None:
         from lbm_inputs import DVM_TABLES as tables
     e, w, c = dvm.dvm2d(name, tables)
-    return Channel(e, w, c, N, Nx, Ny, Kn, g)
+    return Channel(e, w, c, N, Nx, Ny, Kn, g, wall=wall)

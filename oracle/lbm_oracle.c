@@ -35,7 +35,9 @@
  *    rows nearest to it; all rows y < e_y of an incoming a are unknown;
  *  - an outgoing population is credited to the column it lands on,
  *    (x_source + e_x) mod Nx, so Psi is a per-column quantity;
- *  - the force term of Eq. nm.4 is used unchanged for N = 4.
+ *  - the force term of Eq. nm.4 is used unchanged for N = 4;
+ *  - behind wall_mode = 1, the alternative reading of the wall: the condition
+ *    holds for f and fbar follows through Eq. nm.7 (transform_wall_nodes).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -150,6 +152,58 @@ int oracle_collide(const oracle_params* p, const double* f, double* fstar) {
     return 0;
 }
 
+/* Alternative reading of the wall condition (wall_mode = 1): Eq. nm.14 sets
+ * the unknown f_a = Psi rho_w w_a, and fbar follows from f through Eq. nm.7
+ * with the BGK operator and without the force term,
+ *   fbar_a = f_a + (dt / 2 tau) (f_a - f0_a(rho, u)),
+ * rho, u the node's moments (Eq. nm.10).  Those moments contain the unknowns
+ * themselves, so each wall node is solved by fixed-point iteration, starting
+ * from the plain values Psi rho_w w_a already in f (a contraction with factor
+ * ~ dt / 2 tau).  Psi keeps its value from the outgoing flux. */
+static int transform_wall_nodes(const oracle_params* p, double* f) {
+    const int V = p->V, Nx = p->Nx, Ny = p->Ny;
+    const double h = p->dt / (2.0 * p->tau);
+    double* phi = malloc(sizeof(double) * V);
+    int* unk = malloc(sizeof(int) * V);
+    if (!phi || !unk) { free(phi); free(unk); return -1; }
+    for (int y = 0; y < Ny; ++y)
+        for (int x = 0; x < Nx; ++x) {
+            int any = 0;
+            for (int a = 0; a < V; ++a) {
+                const int ys = y - p->ey[a];
+                unk[a] = ys < 0 || ys >= Ny;
+                if (unk[a]) { phi[a] = f[at(p, a, x, y)]; any = 1; }
+            }
+            if (!any) continue;
+            for (int it = 0; it < 100; ++it) {
+                double rho = 0.0, mx = 0.0, my = 0.0;
+                for (int a = 0; a < V; ++a) {
+                    const double fa = f[at(p, a, x, y)];
+                    rho += fa;
+                    mx += fa * p->c * p->ex[a];
+                    my += fa * p->c * p->ey[a];
+                }
+                const double ux = (mx + 0.5 * p->dt * rho * p->gx) / rho;
+                const double uy = (my + 0.5 * p->dt * rho * p->gy) / rho;
+                const double uu = ux * ux + uy * uy;
+                double change = 0.0;
+                for (int a = 0; a < V; ++a) {
+                    if (!unk[a]) continue;
+                    const double s = ux * p->c * p->ex[a] + uy * p->c * p->ey[a];
+                    const double f0 = rho * p->w[a] * f0_over_rho_w(p->N, s, uu);
+                    const double v = (1.0 + h) * phi[a] - h * f0;
+                    const double d = fabs(v - f[at(p, a, x, y)]);
+                    if (d > change) change = d;
+                    f[at(p, a, x, y)] = v;
+                }
+                if (change < 1e-16) break;
+            }
+        }
+    free(phi);
+    free(unk);
+    return 0;
+}
+
 /* Steps (5) and (6): fbar(t+dt) from the post-collision field fstar. */
 int oracle_stream(const oracle_params* p, const double* fstar, double* f) {
     const int V = p->V, Nx = p->Nx, Ny = p->Ny;
@@ -195,6 +249,7 @@ int oracle_stream(const oracle_params* p, const double* fstar, double* f) {
                 f[at(p, a, x, y)] = v;
             }
     free(out_bot);
+    if (p->wall_mode == 1) return transform_wall_nodes(p, f);
     return 0;
 }
 

@@ -12,6 +12,9 @@ typedef struct {
     double tau;                /* relaxation time, units of l0/c0            */
     double dt;                 /* time step = dx / c, dx = 1/Ny              */
     double gx, gy;             /* body acceleration                          */
+    int wall_mode;             /* 0: unknown fbar = Psi rho_w w_a (reading c1);
+                                  1: the wall condition on f, carried to fbar
+                                  through Eq. nm.7 (oracle_stream)            */
 } oracle_params;
 
 /* f, work: V*Ny*Nx doubles, planes [V][Ny][Nx].  f holds fbar before the
