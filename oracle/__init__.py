@@ -54,7 +54,8 @@ class _Params(ctypes.Structure):
                 ("w", ctypes.POINTER(ctypes.c_double)),
                 ("c", ctypes.c_double), ("tau", ctypes.c_double),
                 ("dt", ctypes.c_double), ("gx", ctypes.c_double),
-                ("gy", ctypes.c_double), ("wall_mode", ctypes.c_int)]
+                ("gy", ctypes.c_double), ("wall_mode", ctypes.c_int),
+                ("force_a3", ctypes.c_int)]
 
 
 def _dp(a):
@@ -80,7 +81,7 @@ class Channel:
     c: lattice speed; N: Hermite order; g: body acceleration along x.
     """
 
-    def __init__(self, e, w, c, N, Nx, Ny, Kn, g, gy=0.0, wall="plain"):
+    def __init__(self, e, w, c, N, Nx, Ny, Kn, g, gy=0.0, wall="plain", force="nm4"):
         e = np.asarray(e)
         self.V = len(e)
         self.Nx, self.Ny, self.N = int(Nx), int(Ny), int(N)
@@ -94,7 +95,8 @@ class Channel:
                          self.ex.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                          self.ey.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                          _dp(self.w), self.c, self.tau, self.dt, self.g, float(gy),
-                         {"plain": 0, "transformed": 1}[wall])
+                         {"plain": 0, "transformed": 1}[wall],
+                         {"nm4": 0, "nm4+a3": 1}[force])
         self.f = np.zeros((self.V, self.Ny, self.Nx))
         self.work = np.zeros_like(self.f)
         self.steps = 0
@@ -216,11 +218,13 @@ class Channel:
         return out
 
 
-def channel(name, N, Nx, Ny, Kn, g, tables=None, wall="plain"):
+def channel(name, N, Nx, Ny, Kn, g, tables=None, wall="plain", force="nm4"):
     """Channel for a named DVM (a 2D table, or '<3D name>xz' for the (x, z)
     marginal of a 3D table).  wall: "plain" (the unknown fbar is Psi rho_w w_a)
-    or "transformed" (the condition holds for f, fbar through Eq. nm.7)."""
+    or "transformed" (the condition holds for f, fbar through Eq. nm.7).
+    force: "nm4" (Eq. nm.4 as printed) or, for N = 4, "nm4+a3" (plus the
+    fourth-order Hermite force term with a^(3) = rho u u u)."""
     if tables is None:
         from lbm_inputs import DVM_TABLES as tables
     e, w, c = dvm.dvm2d(name, tables)
-    return Channel(e, w, c, N, Nx, Ny, Kn, g, wall=wall)
+    return Channel(e, w, c, N, Nx, Ny, Kn, g, wall=wall, force=force)

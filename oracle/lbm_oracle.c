@@ -35,7 +35,8 @@
  *    rows nearest to it; all rows y < e_y of an incoming a are unknown;
  *  - an outgoing population is credited to the column it lands on,
  *    (x_source + e_x) mod Nx, so Psi is a per-column quantity;
- *  - the force term of Eq. nm.4 is used unchanged for N = 4;
+ *  - the force term of Eq. nm.4 is used unchanged for N = 4 (behind
+ *    force_a3 = 1, the variant with the fourth-order term of a^(3) = rho uuu);
  *  - behind wall_mode = 1, the alternative reading of the wall: the condition
  *    holds for f and fbar follows through Eq. nm.7 (transform_wall_nodes).
  */
@@ -68,7 +69,7 @@ static double H2(const double xi[2], int i, int j) {
 }
 
 /* Body-force term F_a of Eq. nm.4 for velocity xi (w_a factored in). */
-static double force_term(int N, double rho, const double u[2], const double g[2],
+static double force_term(int N, int a3, double rho, const double u[2], const double g[2],
                          const double Pi[2][2], const double xi[2], double wa) {
     double gxi = g[0] * xi[0] + g[1] * xi[1];
     double uxi = u[0] * xi[0] + u[1] * xi[1];
@@ -81,6 +82,14 @@ static double force_term(int N, double rho, const double u[2], const double g[2]
                 t += (Pi[i][j] - (i == j ? rho : 0.0)) *
                      (gxi * H2(xi, i, j) - 2.0 * g[i] * xi[j]);
         r += t / (2.0 * rho);
+    }
+    if (N >= 4 && a3) {
+        /* (1/3!) g_i a^(3)_jkl H^(4)_ijkl(xi) / rho with a^(3) = rho u u u:
+         * H^(4) = xi^4 - 6 sym(xi xi delta) + 3 sym(delta delta) contracted
+         * with g u u u gives the four terms below. */
+        const double uu = u[0] * u[0] + u[1] * u[1];
+        r += (gxi * uxi * uxi * uxi - 3.0 * gxi * uxi * uu - 3.0 * uxi * uxi * ug +
+              3.0 * ug * uu) / 6.0;
     }
     return rho * wa * r;
 }
@@ -119,14 +128,14 @@ static void collide_node(const oracle_params* p, const double* fin, double* fout
     double Pi[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
     for (int a = 0; a < V; ++a) {
         double xi[2] = {c * p->ex[a], c * p->ey[a]};
-        double feq = f0[a] + tau * force_term(p->N, rho, u, g, Pi0, xi, p->w[a]);
+        double feq = f0[a] + tau * force_term(p->N, p->force_a3, rho, u, g, Pi0, xi, p->w[a]);
         double fa = (2.0 * tau * fin[a] + dt * feq) / (2.0 * tau + dt);
         for (int i = 0; i < 2; ++i)
             for (int j = 0; j < 2; ++j) Pi[i][j] += fa * xi[i] * xi[j];
     }
     for (int a = 0; a < V; ++a) {
         double xi[2] = {c * p->ex[a], c * p->ey[a]};
-        F[a] = force_term(p->N, rho, u, g, Pi, xi, p->w[a]);
+        F[a] = force_term(p->N, p->force_a3, rho, u, g, Pi, xi, p->w[a]);
     }
 
     /* (4) collision, Eq. nm.8 with feq = f0 + tau F (Eq. nm.2) */
@@ -295,6 +304,6 @@ void oracle_force(const oracle_params* p, double rho, double ux, double uy,
     const double Pi[2][2] = {{Pi4[0], Pi4[1]}, {Pi4[2], Pi4[3]}};
     for (int a = 0; a < p->V; ++a) {
         double xi[2] = {p->c * p->ex[a], p->c * p->ey[a]};
-        F[a] = force_term(p->N, rho, u, g, Pi, xi, p->w[a]);
+        F[a] = force_term(p->N, p->force_a3, rho, u, g, Pi, xi, p->w[a]);
     }
 }

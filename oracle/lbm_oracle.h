@@ -15,6 +15,9 @@ typedef struct {
     int wall_mode;             /* 0: unknown fbar = Psi rho_w w_a (reading c1);
                                   1: the wall condition on f, carried to fbar
                                   through Eq. nm.7 (oracle_stream)            */
+    int force_a3;              /* N = 4 only: 0: Eq. nm.4 unchanged (reading c5);
+                                  1: plus the fourth-order Hermite force term
+                                  with a^(3) = rho u u u                      */
 } oracle_params;
 
 /* f, work: V*Ny*Nx doubles, planes [V][Ny][Nx].  f holds fbar before the
