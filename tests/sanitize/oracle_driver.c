@@ -1,6 +1,7 @@
 /* Sanitizer run of the oracle time step (test infrastructure).
- * Reads "V c N Nx Ny Kn g steps" then V lines "ex ey w" from stdin, runs the
- * steps from rho = 1 and prints the relative change of the total mass. */
+ * Reads "V c N Nx Ny Kn g steps wall_mode force_a3" then V lines "ex ey w"
+ * from stdin, runs the steps from rho = 1 and prints the relative change of the
+ * total mass and the centre velocity. */
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -8,16 +9,19 @@
 #include "lbm_oracle.h"
 
 int main(void) {
-    int V, N, Nx, Ny;
+    int V, N, Nx, Ny, wall_mode, force_a3;
     long steps;
     double c, Kn, g;
-    if (scanf("%d %lf %d %d %d %lf %lf %ld", &V, &c, &N, &Nx, &Ny, &Kn, &g, &steps) != 8) return 2;
+    if (scanf("%d %lf %d %d %d %lf %lf %ld %d %d", &V, &c, &N, &Nx, &Ny, &Kn, &g, &steps,
+              &wall_mode, &force_a3) != 10)
+        return 2;
     int* ex = malloc(sizeof(int) * V);
     int* ey = malloc(sizeof(int) * V);
     double* w = malloc(sizeof(double) * V);
     for (int a = 0; a < V; ++a)
         if (scanf("%d %d %lf", &ex[a], &ey[a], &w[a]) != 3) return 2;
-    oracle_params p = {V, Nx, Ny, N, ex, ey, w, c, sqrt(2.0 / M_PI) * Kn, 1.0 / (Ny * c), g, 0.0};
+    oracle_params p = {V, Nx, Ny, N, ex, ey, w, c, sqrt(2.0 / M_PI) * Kn, 1.0 / (Ny * c), g, 0.0,
+                       wall_mode, force_a3};
     const long n = (long)V * Nx * Ny;
     double* f = malloc(sizeof(double) * n);
     double* work = malloc(sizeof(double) * n);

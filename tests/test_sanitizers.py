@@ -38,15 +38,18 @@ def _run(exe, stdin):
 @pytest.mark.skipif(shutil.which("gcc") is None, reason="no gcc")
 @pytest.mark.parametrize("name,N,Nx,Ny", [("D2V16", 3, 3, 8), ("D2V33", 4, 5, 4), ("D2V32", 3, 2, 12),
                                          ("D3V107xz", 3, 7, 6)])
-def test_oracle_step_under_sanitizers(tmp_path, name, N, Nx, Ny):
+@pytest.mark.parametrize("wall_mode,force_a3", [(0, 0), (1, 1)])
+def test_oracle_step_under_sanitizers(tmp_path, name, N, Nx, Ny, wall_mode, force_a3):
+    """Both readings of the wall and of the N = 4 force term; the transformed
+    wall does not conserve mass exactly (a drift of order dt/tau Ma^2)."""
     exe = _build(tmp_path, "gcc", [os.path.join(ROOT, "tests", "sanitize", "oracle_driver.c"),
                                    os.path.join(ROOT, "oracle", "lbm_oracle.c")],
                  [os.path.join(ROOT, "oracle")], "oracle_san")
     e, w, c = dvm.dvm2d(name, DVM_TABLES)
-    lines = [f"{len(w)} {c!r} {N} {Nx} {Ny} 0.3 0.002 40"]
+    lines = [f"{len(w)} {c!r} {N} {Nx} {Ny} 0.3 0.002 40 {wall_mode} {force_a3}"]
     lines += [f"{int(a)} {int(b)} {x!r}" for (a, b), x in zip(e.tolist(), w.tolist())]
     dmass, uc = _run(exe, "\n".join(lines) + "\n")
-    assert float(dmass) < 1e-13 and float(uc) > 0
+    assert float(dmass) < (1e-13 if wall_mode == 0 else 1e-5) and float(uc) > 0
 
 
 @pytest.mark.skipif(shutil.which("g++") is None, reason="no g++")
