@@ -260,7 +260,10 @@ int plan_cluster_t(const KParams<C>& k, int N, int LP, ClusterPlan& pl) {
         c.LP = LP;
         c.nb = nb;
         c.nt = nt;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+        // the limit is per kernel and shared by every solver that uses it: set it
+        // to the device's maximum, so that a later, smaller plan cannot lower it
+        // below what an earlier solver's launches need
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
                 cudaSuccess ||
             cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                 cudaSuccess) {

@@ -140,6 +140,19 @@ def test_config1_fp32_resident_matches_oracle():
     assert abs(s.slip_velocity() / ref.slip_velocity() - 1) < 1e-4
 
 
+def test_resident_solvers_of_different_sizes_coexist():
+    """Two resident solvers of different sizes on the same kernel: planning
+    the second leaves the first stepping bit for bit like its per-step twin."""
+    big = _solver("D2V16", 3, 1, 512, 0.2, True)         # 32 rows per CTA
+    small = _solver("D2V16", 3, 1, 20, 0.2, True)
+    assert big.resident_ctas() > 0 and small.resident_ctas() > 0
+    big_ref = _solver("D2V16", 3, 1, 512, 0.2, False)
+    for s in (big, small, big_ref):
+        s.step(30)
+    assert big.status() == 0
+    assert np.array_equal(big.populations(), big_ref.populations())
+
+
 def test_resident_eligibility():
     """Only fp64 and fp32 channels small enough for one cluster run resident."""
     import paper_1510_08886_gb300 as lbm
