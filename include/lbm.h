@@ -199,6 +199,20 @@ int lbm_set_resident(lbm_solver* s, int enable);
  * disabled).  NULL pointer -> LBM_EINVAL. */
 int lbm_resident_ctas(lbm_solver* s, int* ctas);
 
+/* Time-averaged moments.  The paper's scheme is deterministic; 16-bit
+ * storage with stochastically rounded stores (LBM_FP16, LBM_BF16) is not: its
+ * state settles into a statistical steady state whose snapshots scatter by
+ * the rounding noise (~1e-3 of the flow in u_s at the walls), while time
+ * averages converge to the steady state of the scheme.  lbm_average advances
+ * nsteps steps and samples the fp64 moments rho, u_x, u_y of every `every`-th
+ * of them (floor(nsteps / every) samples); afterwards the moment fields hold
+ * the sample means, so lbm_moments, lbm_mass_flow, lbm_slip_velocity and
+ * lbm_knudsen_layer report time averages (mass flow and slip velocity of the
+ * averaged field, Eq. pf.1 and defSlip) until the next step.  The state
+ * itself is the last step's.  Any precision; one launch per step.
+ * Requires nsteps >= every >= 1, else LBM_EINVAL.  Asynchronous. */
+int lbm_average(lbm_solver* s, long nsteps, long every);
+
 /* Step until max over nodes of |u_x(t) - u_x(t - dt)| < tol, tested every
  * check_every (>= 2) steps, or until max_steps in total.  Returns LBM_OK when
  * converged, LBM_ENOTCONV otherwise; *steps_done and *last_du (either may be
@@ -361,6 +375,17 @@ int lbm_engine_state_bytes(lbm_engine* e, int slot, size_t* bytes);
 int lbm_engine_get_state(lbm_engine* e, int slot, void* host, size_t bytes);
 int lbm_engine_set_state(lbm_engine* e, int slot, const void* host, size_t bytes);
 
+/* ---- measurement helper -------------------------------------------------- */
+
+/* Sustained FMA rate of the current device (no counterpart in the paper: the
+ * roofline denominator of an arithmetic-bound step).  precision: LBM_FP64 or
+ * LBM_FP32 (else LBM_EINVAL).  Launches a grid of 8 blocks per SM, each thread
+ * running 8 independent chains a = a b + c, timed with CUDA events on
+ * `stream` (a cudaStream_t or NULL) after an untimed launch; *flops_per_s is
+ * the best of three, counting 2 flops per FMA.  Allocates and frees a small
+ * device buffer; synchronises the stream.  Takes ~0.1-0.3 s on GB300. */
+int lbm_fma_rate(int precision, void* stream, double* flops_per_s);
+
 /* ---- observables without allocation ------------------------------------ */
 
 /* The paper has no counterpart to this entry point; it exists for callers
@@ -381,12 +406,21 @@ int lbm_engine_set_state(lbm_engine* e, int slot, const void* host, size_t bytes
  * Its scratch is one fixed array of 4096 doubles (32 KiB) in the library's
  * device memory; every GPU that loads the library holds it until the process
  * exits.  The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress, with that device current): make that first call
- * before any stream capture.  Every call on a device shares the array, and a
- * call overwrites every entry it reads before reading it, so nothing carries
- * over from the previous call; calls that overlap on the GPU (other streams,
- * other threads) race on it and must be serialised by the caller.  No
- * cudaMalloc, cudaFree or allocating library routine is called. */
+ * (cudaGetSymbolAddress, with that device current), and so does the first
+ * call after the device's context has changed (e.g. after cudaDeviceReset).
+ * With lazy module loading (the CUDA default) that first call also loads the
+ * library's kernels and the array onto the device, which takes device memory
+ * and may synchronise the device: "allocates nothing" holds from the second
+ * call on a device.  Make that first call before any stream capture, and
+ * again after a context reset.  Every call on a device shares the array, and
+ * a call overwrites every entry it reads before reading it, so nothing
+ * carries over from the previous call; calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ * A CUDA error already pending on the calling thread when the call starts
+ * (from earlier, unrelated work) is left in place for its owner and the call
+ * returns LBM_ECUDA without launching; a launch error of this call is
+ * returned as LBM_ECUDA and cleared. */
 int lbm_observables_noalloc(const double* ux_device, int Nx, int Ny, double Kn,
                             double force, double* out_device, void* stream);
 

@@ -158,6 +158,18 @@ def dvm_augment(e, c, Q, constraints):
     return w, r.value
 
 
+def fma_rate(precision="fp64", stream=None):
+    """Sustained FMA rate of the current device in flop/s (lbm_fma_rate):
+    the measured peak of an arithmetic-bound step."""
+    torch = _torch_cuda()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_double(0)
+    prec = {"fp64": _lib.LBM_FP64, "fp32": _lib.LBM_FP32}[precision]
+    check(_lib.lib().lbm_fma_rate(prec, ctypes.c_void_p(st.cuda_stream), ctypes.byref(out)),
+          "lbm_fma_rate")
+    return out.value
+
+
 def _torch_cuda():
     import torch
     if not torch.cuda.is_available():
@@ -246,6 +258,13 @@ class Solver:
 
     def step(self, n=1):
         check(_lib.lib().lbm_step(self._h, int(n)), "lbm_step")
+        return self
+
+    def average(self, n, every=1):
+        """Advance n steps and leave in the moment fields the mean of the
+        moments of every `every`-th step (lbm_average): the observables then
+        report time averages, the steady state of 16-bit storage."""
+        check(_lib.lib().lbm_average(self._h, int(n), int(every)), "lbm_average")
         return self
 
     def set_resident(self, enable):
@@ -381,6 +400,13 @@ class Engine:
     def set_chunk(self, steps):
         check(_lib.lib().lbm_engine_set_chunk(self._h, int(steps)), "lbm_engine_set_chunk")
         self.chunk = int(steps)
+
+    def average(self, n, every=1):
+        """Advance n steps and leave in the moment fields the mean of the
+        moments of every `every`-th step (lbm_average): the observables then
+        report time averages, the steady state of 16-bit storage."""
+        check(_lib.lib().lbm_average(self._h, int(n), int(every)), "lbm_average")
+        return self
 
     def set_resident(self, enable):
         check(_lib.lib().lbm_engine_set_resident(self._h, int(bool(enable))),

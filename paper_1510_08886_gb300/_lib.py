@@ -53,6 +53,8 @@ SIGNATURES = {
     "lbm_init": (ctypes.c_int, [ctypes.c_void_p, c_double_p]),
     "lbm_init_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_long]),
+    "lbm_average": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_long]),
+    "lbm_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "lbm_set_resident": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_resident_ctas": (ctypes.c_int, [ctypes.c_void_p, c_int_p]),
     "lbm_run_to_steady": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_long,

@@ -43,6 +43,17 @@ constexpr int engine_extra_regs() {
     return SET::R + 2 * SET::P == 53 ? 0 : (SET::P > 20 ? 24 : 12);
 }
 
+// Moments, equilibrium, force and relaxation of one node (register values
+// f in place): the arithmetic of k_step_ct, shared by both engine kernels.
+template <class SET, int N, typename S, typename C>
+__device__ __forceinline__ CellCoef<C> res_collide(const KParams<C>& k, C* f) {
+    C drho, Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
+    moments_ct<SET, S, C>(k, f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, SET::P>{});
+    const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, Kxy, Kyy);
+    relax_ct<SET, N, S, C>(k, q, f);
+    return q;
+}
+
 // emit: 0 = nothing, 1 = rho, u_x, u_y into the moment fields, 2 = u_x into prev
 template <class SET, int N, typename S, typename C>
 __global__ void __launch_bounds__(kBlock, min_blocks_for(SET::R + 2 * SET::P + engine_extra_regs<SET>(),
@@ -102,7 +113,7 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
             C f[V];
             if (fast) {
 #pragma unroll
-                for (int a = 0; a < V; ++a) f[a] = ld_pop<S, C>(k, ld_stream(sp[a] + cell), a);
+                for (int a = 0; a < V; ++a) f[a] = ld_val<S, C>(ld_stream(sp[a] + cell));
             } else if (rows || (cell / k.Nx >= k.maxey && cell / k.Nx < k.Ny - k.maxey)) {
                 // nodes away from the walls (the whole tile, or this node of a wall tile)
                 pull_rows_any<SET, S, C>(k, sp, cell, f);
@@ -111,17 +122,11 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
                 const int x = cell - y * k.Nx;
                 pull_wall_ct<SET, S, C>(k, src, x, y, f, std::make_integer_sequence<int, V>{});
             }
-            C drho = R ? f[0] : C(0), Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
-            moments_ct<SET, C>(f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, P>{});
-            const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, Kxy, Kyy);
-            if (R) f[0] = fma(k.one_m_omega, f[0], k.omw_rest * q.a0);
-            if (k.force)
-                relax_ct<SET, N, true, C>(k, q, f, std::make_integer_sequence<int, P>{});
-            else
-                relax_ct<SET, N, false, C>(k, q, f, std::make_integer_sequence<int, P>{});
-            unsigned rs = sr_seed<S, C>(seed + unsigned(tile.slot) * 0x632be5abu, cell);
+            const CellCoef<C> q = res_collide<SET, N, S, C>(k, f);
+            S out[V];
+            pack_ct<SET, S, C>(f, sr_seed<S, C>(seed + unsigned(tile.slot) * 0x632be5abu, cell), out);
 #pragma unroll
-            for (int a = 0; a < V; ++a) dp[a][cell] = st_pop<S, C>(k, f[a], a, rs);
+            for (int a = 0; a < V; ++a) dp[a][cell] = out[a];
             if (emit == 1) {
                 B.rho[cell] = 1.0 + (double)q.drho;
                 B.ux[cell] = (double)q.ux;
@@ -183,9 +188,11 @@ __host__ __device__ constexpr int set_maxey() {
     return m;
 }
 
-template <class SET>
+// Threads of a resident block: the V populations of a node stay in
+// registers, so fp64 (two registers a value) halves the block.
+template <class SET, typename C = float>
 __host__ __device__ constexpr int res_threads() {
-    return SET::R + 2 * SET::P <= 16 ? 1024 : 512;
+    return (SET::R + 2 * SET::P <= 16 ? 1024 : 512) / (sizeof(C) == 8 ? 2 : 1);
 }
 
 // (x + d) mod Nx for x in [0, Nx); mode 0: Nx = 1, 1: Nx >= |d|, 2: any Nx
@@ -235,12 +242,12 @@ __device__ __forceinline__ C res_wall_value(const KParams<C>& k, const S* sb, in
     constexpr int EY = plane_ey<SET>(A);
     const int Nx = k.Nx;
     const int ys = y - EY;
-    if (ys < 0) return pb * k.cw[A];
-    if (ys >= k.Ny) return pt * k.cw[A];
-    if (STEP_A) return ld_pop<S, C>(k, sb[A * PS + (y + G) * Nx + x], A);
+    if (ys < 0) return fill_val<S, C>(k, pb, A);
+    if (ys >= k.Ny) return fill_val<S, C>(k, pt, A);
+    if (STEP_A) return ld_val<S, C>(sb[A * PS + (y + G) * Nx + x]);
     int xs = x - k.sx[A];
     xs += (xs < 0) ? Nx : 0;
-    return ld_pop<S, C>(k, sb[plane_opp<SET>(A) * PS + (ys + G) * Nx + xs], A);
+    return ld_val<S, C>(sb[plane_opp<SET>(A) * PS + (ys + G) * Nx + xs]);
 }
 
 template <class SET, typename S, typename C, bool STEP_A, int... I>
@@ -259,10 +266,10 @@ __device__ __forceinline__ void res_pull(const KParams<C>& k, const S* sb, int P
     const int Nx = k.Nx;
     if constexpr (STEP_A) {
         const int o = (y + G) * Nx + x;
-        ((f[I] = ld_pop<S, C>(k, sb[I * PS + o], I)), ...);
+        ((f[I] = ld_val<S, C>(sb[I * PS + o])), ...);
     } else {
-        ((f[I] = ld_pop<S, C>(k, sb[plane_opp<SET>(I) * PS + (y - plane_ey<SET>(I) + G) * Nx +
-                                    xwrap<-plane_ex<SET>(I), MODE>(x, Nx)], I)), ...);
+        ((f[I] = ld_val<S, C>(sb[plane_opp<SET>(I) * PS + (y - plane_ey<SET>(I) + G) * Nx +
+                                 xwrap<-plane_ex<SET>(I), MODE>(x, Nx)])), ...);
     }
 }
 
@@ -271,29 +278,15 @@ __device__ __forceinline__ void res_push(const KParams<C>& k, S* sb, int PS, int
                                          unsigned rs, std::integer_sequence<int, I...>) {
     constexpr int G = set_maxey<SET>();
     const int Nx = k.Nx;
+    S out[sizeof...(I)];
+    pack_ct<SET, S, C>(f, rs, out);
     if constexpr (STEP_A) {
         const int o = (y + G) * Nx + x;
-        ((sb[plane_opp<SET>(I) * PS + o] = st_pop<S, C>(k, f[I], I, rs)), ...);
+        ((sb[plane_opp<SET>(I) * PS + o] = out[I]), ...);
     } else {
         ((sb[I * PS + (y + plane_ey<SET>(I) + G) * Nx + xwrap<plane_ex<SET>(I), MODE>(x, Nx)] =
-              st_pop<S, C>(k, f[I], I, rs)), ...);
+              out[I]), ...);
     }
-}
-
-// Moments, equilibrium, force and relaxation of one node (f in place): the
-// arithmetic of k_engine_step.
-template <class SET, int N, typename C>
-__device__ __forceinline__ CellCoef<C> res_collide(const KParams<C>& k, C* f) {
-    constexpr int R = SET::R, P = SET::P;
-    C drho = R ? f[0] : C(0), Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
-    moments_ct<SET, C>(f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, P>{});
-    const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, Kxy, Kyy);
-    if (R) f[0] = fma(k.one_m_omega, f[0], k.omw_rest * q.a0);
-    if (k.force)
-        relax_ct<SET, N, true, C>(k, q, f, std::make_integer_sequence<int, P>{});
-    else
-        relax_ct<SET, N, false, C>(k, q, f, std::make_integer_sequence<int, P>{});
-    return q;
 }
 
 template <typename C>
@@ -331,7 +324,7 @@ __device__ __forceinline__ void res_node(const EngineSolve<C>& B, S* sb, int PS,
     } else {
         res_pull_wall<SET, S, C, STEP_A>(k, sb, PS, x, y, f, std::make_integer_sequence<int, V>{});
     }
-    const CellCoef<C> q = res_collide<SET, N, C>(k, f);
+    const CellCoef<C> q = res_collide<SET, N, S, C>(k, f);
     const unsigned rs = sr_seed<S, C>(seed + unsigned(slot) * 0x632be5abu, cell);
     if (mode == 0)
         res_push<SET, S, C, 0, STEP_A>(k, sb, PS, x, y, f, rs, std::make_integer_sequence<int, V>{});
@@ -346,13 +339,13 @@ __device__ __forceinline__ void res_node(const EngineSolve<C>& B, S* sb, int PS,
 // bundle runs K (even) steps: B, A, B, A, ...  Step i uses the seed and the
 // emit flags of step i of the tiled chunk.
 template <class SET, int N, typename S, typename C>
-__global__ void __launch_bounds__(res_threads<SET>(), 1)
+__global__ void __launch_bounds__(res_threads<SET, C>(), 1)
 k_engine_resident(const EngineSolve<C>* __restrict__ solves, const ResBundle* __restrict__ bundles,
                   const ResChannel* __restrict__ chans, const int* __restrict__ nbundles_p,
                   const int* __restrict__ bundle_off_p, int* __restrict__ counter,
                   const unsigned* __restrict__ seed_p, int K) {
     constexpr int R = SET::R, P = SET::P, V = R + 2 * P, G = set_maxey<SET>();
-    constexpr int BT = res_threads<SET>();
+    constexpr int BT = res_threads<SET, C>();
     constexpr int NPT = kResNodes / BT;
     extern __shared__ __align__(16) unsigned char res_smem[];
     S* const sm = reinterpret_cast<S*>(res_smem);

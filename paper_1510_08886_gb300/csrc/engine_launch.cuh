@@ -1,13 +1,20 @@
 // Launchers of the engine kernels for one storage type (instantiated in
-// engine_fp32.cu and engine_fp16.cu).
+// engine_fp32.cu, engine_fp16.cu, engine_bf16.cu, engine_fp64.cu and the
+// engine_res_*.cu files).
 #pragma once
 
 #include "engine_kernels.cuh"
 
 namespace lbm {
 
+// Compute type of a storage type: fp64 storage computes in fp64, every
+// other format in fp32.
+template <typename S> struct ComputeOf { using type = float; };
+template <> struct ComputeOf<double> { using type = double; };
+template <typename S> using CompOf = typename ComputeOf<S>::type;
+
 struct EngineLaunch {
-    const void* solves;        // EngineSolve<float>*
+    const void* solves;        // EngineSolve<C>* (C the compute type)
     const EngineTile* tiles;   // all tiles
     const int* ntiles;         // device count of this group's tiles
     const int* tile_off;       // device offset of this group's tiles
@@ -19,8 +26,9 @@ struct EngineLaunch {
 
 template <class SET, int N, typename S>
 cudaError_t engine_step_one(const EngineLaunch& L, cudaStream_t st) {
-    k_engine_step<SET, N, S, float><<<L.grid, kBlock, 0, st>>>(
-        static_cast<const EngineSolve<float>*>(L.solves), L.tiles, L.ntiles, L.tile_off, L.counter, L.seed,
+    using C = CompOf<S>;
+    k_engine_step<SET, N, S, C><<<L.grid, kBlock, 0, st>>>(
+        static_cast<const EngineSolve<C>*>(L.solves), L.tiles, L.ntiles, L.tile_off, L.counter, L.seed,
         L.parity, L.emit, L.chunk);
     return cudaGetLastError();
 }
@@ -49,7 +57,7 @@ cudaError_t engine_step_t(int set_id, int N, const EngineLaunch& L, cudaStream_t
 }
 
 struct ResidentLaunch {
-    const void* solves;        // EngineSolve<float>*
+    const void* solves;        // EngineSolve<C>*
     const ResBundle* bundles;  // all bundles (each group's largest first)
     const ResChannel* chans;
     const int* nbundles;       // device count of this group's bundles
@@ -63,13 +71,14 @@ struct ResidentLaunch {
 
 template <class SET, int N, typename S>
 const void* resident_fn() {
-    return reinterpret_cast<const void*>(&k_engine_resident<SET, N, S, float>);
+    return reinterpret_cast<const void*>(&k_engine_resident<SET, N, S, CompOf<S>>);
 }
 
 template <class SET, int N, typename S>
 cudaError_t resident_one(const ResidentLaunch& L, cudaStream_t st) {
-    k_engine_resident<SET, N, S, float><<<L.grid, res_threads<SET>(), L.smem, st>>>(
-        static_cast<const EngineSolve<float>*>(L.solves), L.bundles, L.chans, L.nbundles, L.bundle_off, L.counter,
+    using C = CompOf<S>;
+    k_engine_resident<SET, N, S, C><<<L.grid, res_threads<SET, C>(), L.smem, st>>>(
+        static_cast<const EngineSolve<C>*>(L.solves), L.bundles, L.chans, L.nbundles, L.bundle_off, L.counter,
         L.seed, L.K);
     return cudaGetLastError();
 }
@@ -85,8 +94,8 @@ int resident_attr_one(size_t smem) {
         return 0;
     }
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_engine_resident<SET, N, S, float>,
-                                                      res_threads<SET>(), smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_engine_resident<SET, N, S, CompOf<S>>,
+                                                      res_threads<SET, CompOf<S>>(), smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -136,7 +145,7 @@ int engine_resident_attr_t(int set_id, int N, size_t smem) {
 template <class SET, int N, typename S>
 int engine_occ_one() {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_engine_step<SET, N, S, float>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_engine_step<SET, N, S, CompOf<S>>, kBlock, 0);
     return b;
 }
 

@@ -208,7 +208,17 @@ void fill_params_impl(const lbm::SolveSpec* s, KParams<C>& k) {
         k.peyy[p] = C(y * y);
         k.pge[p] = C(s->c * s->g * x);
         k.pomw[p] = C(omega * s->w[a]);
+        const double ws = s->w[a] * s->scale;
+        k.hw[p] = C(ws);
+        k.hwx[p] = C(ws * x);
+        k.hwy[p] = C(ws * y);
+        k.hwxx[p] = C(ws * x * x);
+        k.hwxy[p] = C(ws * x * y);
+        k.hwyy[p] = C(ws * y * y);
     }
+    k.hw_rest = C(s->R ? s->w[0] * s->scale : 0.0);
+    k.fill_h = C(1.0 / s->scale);
+    k.om_s = C(omega / s->scale);
     k.omw_rest = C(s->R ? omega * s->w[0] : 0.0);
     k.c = C(s->c);
     k.c2 = C(s->c * s->c);
@@ -384,7 +394,7 @@ k_knudsen_layer(const double* __restrict__ ux, int Nx, int Ny, double* __restric
     }
 }
 
-int launch_step(lbm_solver* s, bool emit) {
+int launch_step(lbm_solver* s, int emit) {
     const void* src = static_cast<const char*>(s->b.f[s->cur]);
     void* dst = s->b.f[1 - s->cur];
     set_plane_pointers(s, s->k64, src, dst);
@@ -727,6 +737,34 @@ int lbm_step(lbm_solver* s, long nsteps) {
         if (rc) return rc;
     }
     return LBM_OK;
+}
+
+__global__ void k_scale3(double* a, double* b, double* c, long long n, double f) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        a[i] *= f;
+        b[i] *= f;
+        c[i] *= f;
+    }
+}
+
+int lbm_average(lbm_solver* s, long nsteps, long every) {
+    if (!s || every < 1 || nsteps < every) return LBM_EINVAL;
+    const long long n = (long long)s->Nx * s->Ny;
+    cudaError_t e = cudaSuccess;
+    for (double* f : {s->b.rho, s->b.ux, s->b.uy})
+        if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, size_t(n) * 8, s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    long count = 0;
+    for (long i = 1; i <= nsteps; ++i) {
+        const bool sample = i % every == 0;
+        const int rc = launch_step(s, sample ? 2 : 0);
+        if (rc) return rc;
+        count += sample;
+    }
+    const int blocks = int(std::min<long long>((n + 255) / 256, 4 * 152));
+    k_scale3<<<blocks, 256, 0, s->stream>>>(s->b.rho, s->b.ux, s->b.uy, n, 1.0 / double(count));
+    return cuda_status(cudaGetLastError());
 }
 
 int lbm_run_to_steady(lbm_solver* s, double tol, long max_steps, long check_every,

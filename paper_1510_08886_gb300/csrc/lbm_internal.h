@@ -39,7 +39,7 @@ struct KParams {
     int maxex;                   // max |e_x|
     int set_id;                  // compiled velocity set (dvm_sets.h), -1: generic
     int force;                   // 1 if g != 0
-    int emit;                    // 1: write fp64 rho, u of this step
+    int emit;                    // 1: write fp64 rho, u of this step; 2: add them
     unsigned int seed;           // step counter: stochastic rounding of 16-bit stores
     long long plane;             // elements per plane = ncell
     int ex[LBM_MAX_V], ey[LBM_MAX_V];
@@ -56,6 +56,13 @@ struct KParams {
     // 16-bit storage only: stored h_a = d_a / (w_a S), S a per-solve power of 2
     C sw[LBM_MAX_V];             // w_a S      (load:  d = h * sw)
     C isw[LBM_MAX_V];            // 1/(w_a S)  (store: h = d * isw)
+    // 16-bit storage, compiled velocity sets: the kernels keep h itself in
+    // registers; the moment sums of d = w S h weigh h with these (pair p):
+    C hw[kMaxPairs], hwx[kMaxPairs], hwy[kMaxPairs];        // w S, w S e_x, w S e_y
+    C hwxx[kMaxPairs], hwxy[kMaxPairs], hwyy[kMaxPairs];    // w S e_x^2, w S e_x e_y, w S e_y^2
+    C hw_rest;                   // w_rest S
+    C fill_h;                    // 1/S: the wall fill dPsi w_a in units of w_a S
+    C om_s;                      // omega / S: relaxation target in units of w_a S
     double inv_den;              // 1 / sum_{e_y > 0} e_y w  (= same for e_y < 0)
     // per pair p, positive member e = (ex, ey):
     C pex[kMaxPairs], pey[kMaxPairs];

@@ -48,6 +48,10 @@ template <> __device__ __forceinline__ float cinf<float>() { return HUGE_VALF; }
 template <typename S> struct Storage {
     static constexpr bool scaled = false;
 };
+//
+// The compiled-set kernels round two values at once with the hardware's
+// stochastically rounding conversion (cvt.rs, random bits supplied by the
+// caller): a in the upper half of the result, b in the lower half.
 template <> struct Storage<__half> {
     static constexpr bool scaled = true;
     static __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
@@ -55,6 +59,12 @@ template <> struct Storage<__half> {
     // fp32 keeps 13 more mantissa bits than fp16
     static __device__ __forceinline__ __half from_f_sr(float v, unsigned r) {
         return __float2half_rz(__uint_as_float(__float_as_uint(v) + (r >> 19)));
+    }
+    static __device__ __forceinline__ void sr2(float a, float b, unsigned r, __half& ha, __half& hb) {
+        unsigned d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(r));
+        ha = __ushort_as_half((unsigned short)(d >> 16));
+        hb = __ushort_as_half((unsigned short)(d & 0xffffu));
     }
 };
 template <> struct Storage<__nv_bfloat16> {
@@ -64,6 +74,13 @@ template <> struct Storage<__nv_bfloat16> {
     // bf16 is the upper half of fp32
     static __device__ __forceinline__ __nv_bfloat16 from_f_sr(float v, unsigned r) {
         return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r >> 16)) >> 16));
+    }
+    static __device__ __forceinline__ void sr2(float a, float b, unsigned r, __nv_bfloat16& ha,
+                                               __nv_bfloat16& hb) {
+        unsigned d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(r));
+        ha = __ushort_as_bfloat16((unsigned short)(d >> 16));
+        hb = __ushort_as_bfloat16((unsigned short)(d & 0xffffu));
     }
 };
 
@@ -92,7 +109,7 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 // Interior population load through the read-only path with a 256-byte L2
 // prefetch size: a warp's 128-byte access also brings the next 128 bytes of
 // the plane into L2, which the neighbouring warp reads next (measured +0.35 %
-// on the 4096 x 512 fp32 step).  16-bit storage takes a plain load.
+// on the 4096 x 512 fp32 step).
 __device__ __forceinline__ float ld_stream(const float* p) {
     float v;
     asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
@@ -103,9 +120,17 @@ __device__ __forceinline__ double ld_stream(const double* p) {
     asm("ld.global.nc.L2::256B.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 }
-template <typename S>
-__device__ __forceinline__ S ld_stream(const S* p) {
-    return *p;
+// 16-bit planes: a warp's load is only 64 bytes, so the 256-byte L2 fill
+// brings the next three warps' data as well
+__device__ __forceinline__ __half ld_stream(const __half* p) {
+    unsigned short v;
+    asm("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    return __ushort_as_half(v);
+}
+__device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16* p) {
+    unsigned short v;
+    asm("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
+    return __ushort_as_bfloat16(v);
 }
 
 template <typename S, typename C>
@@ -122,6 +147,22 @@ __device__ __forceinline__ S st_pop(const KParams<C>& k, C v, int a, unsigned& r
     } else {
         return S(v);
     }
+}
+
+// Register value of a stored population in the compiled-set kernels: the
+// deviation d itself for fp64/fp32 storage, h = d / (w_a S) for the 16-bit
+// formats (their moment sums weigh h with w_a S, their relaxation works in h).
+template <typename S, typename C>
+__device__ __forceinline__ C ld_val(S v) {
+    if constexpr (Storage<S>::scaled) return Storage<S>::to_f(v);
+    else return C(v);
+}
+
+// Wall fill d_a = dPsi w_a in register units (dPsi / S for 16-bit storage).
+template <typename S, typename C>
+__device__ __forceinline__ C fill_val(const KParams<C>& k, C dpsi, int a) {
+    if constexpr (Storage<S>::scaled) return mul_rn(dpsi, k.fill_h);
+    else return mul_rn(dpsi, k.cw[a]);
 }
 
 // fp64 sum of the wall terms in a fixed order: term k goes to accumulator
@@ -397,10 +438,18 @@ __device__ __forceinline__ void store_moments(const CellCoef<C>& q, int cell, co
     b.uy[cell] = (double)q.uy;
 }
 
+// emit 1: write the fp64 moments of this step; emit 2: add them to the
+// fields (time averages, lbm_average)
 template <typename C>
 __device__ __forceinline__ void emit_moments(const KParams<C>& k, const CellCoef<C>& q, int cell,
                                              const DevBufs& b) {
-    if (k.emit) store_moments<C>(q, cell, b);
+    if (k.emit == 1) {
+        store_moments<C>(q, cell, b);
+    } else if (k.emit == 2) {
+        b.rho[cell] += 1.0 + (double)q.drho;
+        b.ux[cell] += (double)q.ux;
+        b.uy[cell] += (double)q.uy;
+    }
 }
 
 // Pull one population of plane a into node (x, y) of an interior row.
@@ -418,9 +467,11 @@ __device__ __forceinline__ C wall_value(const KParams<C>& k, const S* __restrict
                                         C pb, C pt) {
     constexpr int EY = A < SET::R ? 0 : (A < SET::R + SET::P ? SET::ey[A - SET::R] : -SET::ey[A - SET::R - SET::P]);
     const int ys = y - EY;
-    if (ys < 0) return pb * k.cw[A];
-    if (ys >= k.Ny) return pt * k.cw[A];
-    return pull<S, C>(k, src, A, x, y);
+    if (ys < 0) return fill_val<S, C>(k, pb, A);
+    if (ys >= k.Ny) return fill_val<S, C>(k, pt, A);
+    int xs = x - k.sx[A];
+    xs += (xs < 0) ? k.Nx : 0;
+    return ld_val<S, C>(src[(long long)A * k.plane + (long long)ys * k.Nx + xs]);
 }
 
 template <class SET, typename S, typename C, int... I>
@@ -469,43 +520,284 @@ __device__ __forceinline__ void moment_pair(C fp, C fm, C& drho, C& Jx, C& Jy, C
     Kyy = fmac<EY * EY>(Kyy, sum);
 }
 
-// Relax the pair (+e, -e), e = (EX, EY) known at compile time; same
-// arithmetic as pair_update with the force along x.
-template <int EX, int EY, int N, bool FORCE, typename C>
-__device__ __forceinline__ void pair_update_ct(const CellCoef<C>& q, C omw, C omo, C& fp, C& fm) {
+// The same sums from h = d / (w S) (16-bit storage): d = w S h, so every
+// term is weighed with the pair's w S e... constants.
+template <int EX, int EY, typename C>
+__device__ __forceinline__ void moment_pair_h(const KParams<C>& k, int p, C fp, C fm, C& drho,
+                                              C& Jx, C& Jy, C& Kxx, C& Kxy, C& Kyy) {
+    const C sum = fp + fm, dif = fp - fm;
+    drho = fma(k.hw[p], sum, drho);
+    if constexpr (EX != 0) Jx = fma(k.hwx[p], dif, Jx);
+    if constexpr (EY != 0) Jy = fma(k.hwy[p], dif, Jy);
+    if constexpr (EX != 0) Kxx = fma(k.hwxx[p], sum, Kxx);
+    if constexpr (EX * EY != 0) Kxy = fma(k.hwxy[p], sum, Kxy);
+    if constexpr (EY != 0) Kyy = fma(k.hwyy[p], sum, Kyy);
+}
+
+// Deviation moments drho = sum d, J = sum d e, K = sum d e e of the node's
+// register values (d, or h for 16-bit storage).
+template <class SET, typename S, typename C, int... I>
+__device__ __forceinline__ void moments_ct(const KParams<C>& k, const C* f, C& drho, C& Jx, C& Jy,
+                                           C& Kxx, C& Kxy, C& Kyy, std::integer_sequence<int, I...>) {
+    if constexpr (Storage<S>::scaled) {
+        drho = SET::R ? mul_rn(k.hw_rest, f[0]) : C(0);
+        (moment_pair_h<SET::ex[I], SET::ey[I], C>(k, I, f[SET::R + I], f[SET::R + SET::P + I], drho,
+                                                  Jx, Jy, Kxx, Kxy, Kyy), ...);
+    } else {
+        drho = SET::R ? f[0] : C(0);
+        (moment_pair<SET::ex[I], SET::ey[I], C>(f[SET::R + I], f[SET::R + SET::P + I], drho, Jx, Jy,
+                                                Kxx, Kxy, Kyy), ...);
+    }
+}
+
+// ---- relaxation of a compiled set: the target as polynomials in e -----------
+// With s = (c u).e and t = s^2, the relaxation target of Eq. nm.3 / nm.4
+// (feq/w - 1 = even + odd part, as in pair_update) is a polynomial in the
+// integer components (ex, ey) of the positive pair member:
+//   Ge = c00 + c20 ex^2 + c11 ex ey + c02 ey^2
+//        + c40 ex^4 + c31 ex^3 ey + c22 ex^2 ey^2 + c13 ex ey^3 + c04 ey^4
+//   Go = d10 ex + d01 ey + d30 ex^3 + d21 ex^2 ey + d12 ex ey^2 + d03 ey^3
+// whose node coefficients follow from expanding a0 + a1 t + a2 t^2 and
+// s (b0 + b1 t) in X = c u_x, Y = c u_y, plus the force terms (g along x):
+// tau rho (g.xi) s adds trcg X to c20 and trcg Y to c11; the odd force part
+// e_x (k0 + cqxx ex^2 + 2 cqxy ex ey + cqyy ey^2) - (hx ex + hy ey) adds
+// k0 - hx to d10, cqxx to d30, 2 cqxy to d21, cqyy to d12 and -hy to d01.
+// Per pair the integer powers of e are compile-time constants, so the force
+// costs nothing per population, and the pairs that share (|ex|, |ey|) share
+// their partial sums:  Ge = Ee + sx sy Eo,  Go = sx Ox + sy Oy  with
+// sx, sy the signs of ex, ey and Ee, Eo, Ox, Oy the parts of Ge, Go even in
+// both, odd in both, odd in ex only, odd in ey only.
+template <typename C>
+struct PolyCoef {
+    C c00, c20, c11, c02, c40, c31, c22, c13, c04;
+    C d10, d01, d30, d21, d12, d03;
+};
+
+// sc scales every coefficient (1: deviation units; omega / S: 16-bit units)
+template <int N, bool FORCE, bool SCALE, typename C>
+__device__ __forceinline__ PolyCoef<C> poly_coef(const CellCoef<C>& q, C sc) {
+    const C X = q.utx, Y = q.uty;
+    const C X2 = mul_rn(X, X), Y2 = mul_rn(Y, Y), XY = mul_rn(X, Y);
+    PolyCoef<C> p{};
+    p.c00 = q.a0;
+    p.c20 = mul_rn(q.a1, X2);
+    p.c11 = mul_rn(C(2) * q.a1, XY);
+    p.c02 = mul_rn(q.a1, Y2);
+    if constexpr (FORCE) {
+        p.c20 = fma(q.trcg, X, p.c20);
+        p.c11 = fma(q.trcg, Y, p.c11);
+    }
+    if constexpr (N >= 4) {
+        const C a2 = q.a2;
+        p.c40 = mul_rn(a2, mul_rn(X2, X2));
+        p.c31 = mul_rn(C(4) * a2, mul_rn(X2, XY));
+        p.c22 = mul_rn(C(6) * a2, mul_rn(X2, Y2));
+        p.c13 = mul_rn(C(4) * a2, mul_rn(XY, Y2));
+        p.c04 = mul_rn(a2, mul_rn(Y2, Y2));
+    }
+    p.d10 = mul_rn(q.b0, X);
+    p.d01 = mul_rn(q.b0, Y);
+    if constexpr (N >= 3) {
+        const C b1 = q.b1;
+        p.d30 = mul_rn(b1, mul_rn(X, X2));
+        p.d21 = mul_rn(C(3) * b1, mul_rn(X2, Y));
+        p.d12 = mul_rn(C(3) * b1, mul_rn(X, Y2));
+        p.d03 = mul_rn(b1, mul_rn(Y, Y2));
+    }
+    if constexpr (FORCE) {
+        p.d10 = p.d10 + (q.k0 - q.hx);
+        p.d01 = p.d01 - q.hy;
+        if constexpr (N >= 3) {
+            p.d30 = p.d30 + q.cqxx;
+            p.d21 = p.d21 + C(2) * q.cqxy;
+            p.d12 = p.d12 + q.cqyy;
+        }
+    }
+    if constexpr (SCALE) {
+        C* v = &p.c00;
+#pragma unroll
+        for (int i = 0; i < 15; ++i) v[i] = mul_rn(v[i], sc);
+    }
+    return p;
+}
+
+template <int K, typename C>
+__device__ __forceinline__ C muli(C v) {          // K v, K > 0
+    if constexpr (K == 1) return v;
+    else return mul_rn(C(K), v);
+}
+
+template <int K, typename C>
+__device__ __forceinline__ C fmai(C a, C v) {     // a + K v, K >= 0
+    if constexpr (K == 0) return a;
+    else if constexpr (K == 1) return a + v;
+    else return fma(C(K), v, a);
+}
+
+// Parts of Ge, Go for |ex| = AX, |ey| = AY (see PolyCoef).
+template <int AX, int AY, int N, typename C>
+struct PolyParts {
+    C Ee, Eo, Ox, Oy;
+    __device__ __forceinline__ explicit PolyParts(const PolyCoef<C>& p) {
+        Ee = fmai<AX * AX>(p.c00, p.c20);
+        Ee = fmai<AY * AY>(Ee, p.c02);
+        if constexpr (N >= 4) {
+            Ee = fmai<AX * AX * AX * AX>(Ee, p.c40);
+            Ee = fmai<AX * AX * AY * AY>(Ee, p.c22);
+            Ee = fmai<AY * AY * AY * AY>(Ee, p.c04);
+        }
+        Eo = C(0);
+        if constexpr (AX * AY != 0) {
+            Eo = muli<AX * AY>(p.c11);
+            if constexpr (N >= 4) {
+                Eo = fmai<AX * AX * AX * AY>(Eo, p.c31);
+                Eo = fmai<AX * AY * AY * AY>(Eo, p.c13);
+            }
+        }
+        Ox = C(0);
+        if constexpr (AX != 0) {
+            Ox = muli<AX>(p.d10);
+            if constexpr (N >= 3) {
+                Ox = fmai<AX * AX * AX>(Ox, p.d30);
+                Ox = fmai<AX * AY * AY>(Ox, p.d12);
+            }
+        }
+        Oy = C(0);
+        if constexpr (AY != 0) {
+            Oy = muli<AY>(p.d01);
+            if constexpr (N >= 3) {
+                Oy = fmai<AX * AX * AY>(Oy, p.d21);
+                Oy = fmai<AY * AY * AY>(Oy, p.d03);
+            }
+        }
+    }
+};
+
+__host__ __device__ constexpr int iabs(int v) { return v < 0 ? -v : v; }
+
+// First pair of a compiled set with the same (|ex|, |ey|) as pair p.
+template <class SET>
+__host__ __device__ constexpr int poly_class(int p) {
+    for (int q = 0; q < p; ++q)
+        if (iabs(SET::ex[q]) == iabs(SET::ex[p]) && iabs(SET::ey[q]) == iabs(SET::ey[p])) return q;
+    return p;
+}
+
+// Relax pair J (a member of the class of pair P0) from the class's parts.
+// Deviation units: d* = (1 - omega) d + omega w (Ge +- Go); 16-bit units
+// (coefficients already times omega / S): h* = (1 - omega) h + (Ge +- Go).
+template <class SET, int J, bool HSPACE, typename C, class PARTS>
+__device__ __forceinline__ void poly_pair(const KParams<C>& k, const PARTS& pp, C* f) {
+    constexpr int EX = SET::ex[J], EY = SET::ey[J];
+    constexpr bool nx = EX < 0, ny = EY < 0;
+    const C Ge = (nx != ny) ? pp.Ee - pp.Eo : pp.Ee + pp.Eo;
+    C Go;
+    if constexpr (EX == 0) Go = ny ? -pp.Oy : pp.Oy;
+    else if constexpr (EY == 0) Go = nx ? -pp.Ox : pp.Ox;
+    else Go = nx ? (ny ? -(pp.Ox + pp.Oy) : pp.Oy - pp.Ox) : (ny ? pp.Ox - pp.Oy : pp.Ox + pp.Oy);
+    C& fp = f[SET::R + J];
+    C& fm = f[SET::R + SET::P + J];
+    const C omo = k.one_m_omega;
+    if constexpr (HSPACE) {
+        fp = fma(omo, fp, Ge + Go);
+        fm = fma(omo, fm, Ge - Go);
+    } else {
+        const C omw = k.pomw[J];
+        const C Xe = mul_rn(omw, Ge);
+        fp = fma(omo, fp, fma(omw, Go, Xe));
+        fm = fma(omo, fm, fma(-omw, Go, Xe));
+    }
+}
+
+template <class SET, int P0, int N, bool HSPACE, typename C, int... J>
+__device__ __forceinline__ void poly_class_relax(const KParams<C>& k, const PolyCoef<C>& pc, C* f,
+                                                 std::integer_sequence<int, J...>) {
+    if constexpr (poly_class<SET>(P0) == P0) {
+        const PolyParts<iabs(SET::ex[P0]), iabs(SET::ey[P0]), N, C> pp(pc);
+        ((poly_class<SET>(J) == P0 ? poly_pair<SET, J, HSPACE, C>(k, pp, f) : void()), ...);
+    }
+}
+
+template <class SET, int N, bool HSPACE, typename C, int... I>
+__device__ __forceinline__ void poly_relax_all(const KParams<C>& k, const PolyCoef<C>& pc, C* f,
+                                               std::integer_sequence<int, I...> seq) {
+    (poly_class_relax<SET, I, N, HSPACE, C>(k, pc, f, seq), ...);
+}
+
+// Force-free relaxation of the pair (+e, -e), e = (EX, EY) known at compile
+// time, in the per-pair form: s = (c u).e, t = s^2, Ge = a0 + t (a1 + t a2),
+// Go = s (b0 + t b1).  Without the force terms this costs fewer operations
+// per pair than the polynomial form's shared partial sums.
+template <int EX, int EY, int N, bool HSPACE, typename C>
+__device__ __forceinline__ void pair_update_free(const CellCoef<C>& q, C omw, C omo, C sc, C& fp,
+                                                 C& fm) {
     const C s = lin<EX, EY>(q.utx, q.uty);
     const C t = mul_rn(s, s);
-    C Ge = N >= 4 ? fma(t, fma(t, q.a2, q.a1), q.a0) : fma(t, q.a1, q.a0);
-    C Go = N >= 3 ? mul_rn(s, fma(t, q.b1, q.b0)) : mul_rn(s, q.b0);
-    if constexpr (FORCE) {
-        if constexpr (EX != 0) {
-            // even: tau rho (g.xi) s; odd: (g.xi)(tau rho + (tau/2) Q)
-            Ge = fma(mulc<EX>(q.trcg), s, Ge);
-            C inner = q.k0;
-            inner = fmac<EX * EX>(inner, q.cqxx);
-            inner = fmac<2 * EX * EY>(inner, q.cqxy);
-            inner = fmac<EY * EY>(inner, q.cqyy);
-            Go = fmac<EX>(Go, inner);
-        }
-        Go = Go - lin<EX, EY>(q.hx, q.hy);      // - tau (g.A).xi
+    const C Ge = N >= 4 ? fma(t, fma(t, q.a2, q.a1), q.a0) : fma(t, q.a1, q.a0);
+    const C Go = N >= 3 ? mul_rn(s, fma(t, q.b1, q.b0)) : mul_rn(s, q.b0);
+    if constexpr (HSPACE) {          // sc = omega / S
+        const C Xe = mul_rn(sc, Ge);
+        fp = fma(omo, fp, fma(sc, Go, Xe));
+        fm = fma(omo, fm, fma(-sc, Go, Xe));
+    } else {
+        const C Xe = mul_rn(omw, Ge);
+        fp = fma(omo, fp, fma(omw, Go, Xe));
+        fm = fma(omo, fm, fma(-omw, Go, Xe));
     }
-    const C X = mul_rn(omw, Ge);
-    fp = fma(omo, fp, fma(omw, Go, X));
-    fm = fma(omo, fm, fma(-omw, Go, X));
 }
 
-template <class SET, typename C, int... I>
-__device__ __forceinline__ void moments_ct(const C* f, C& drho, C& Jx, C& Jy, C& Kxx, C& Kxy,
-                                           C& Kyy, std::integer_sequence<int, I...>) {
-    (moment_pair<SET::ex[I], SET::ey[I], C>(f[SET::R + I], f[SET::R + SET::P + I], drho, Jx, Jy,
-                                            Kxx, Kxy, Kyy), ...);
+template <class SET, int N, bool HSPACE, typename C, int... I>
+__device__ __forceinline__ void relax_free_all(const KParams<C>& k, const CellCoef<C>& q, C* f,
+                                               std::integer_sequence<int, I...>) {
+    const C sc = HSPACE ? k.om_s : C(1);
+    (pair_update_free<SET::ex[I], SET::ey[I], N, HSPACE, C>(q, k.pomw[I], k.one_m_omega, sc,
+                                                            f[SET::R + I], f[SET::R + SET::P + I]),
+     ...);
 }
 
-template <class SET, int N, bool FORCE, typename C, int... I>
-__device__ __forceinline__ void relax_ct(const KParams<C>& k, const CellCoef<C>& q, C* f,
-                                         std::integer_sequence<int, I...>) {
-    (pair_update_ct<SET::ex[I], SET::ey[I], N, FORCE, C>(q, k.pomw[I], k.one_m_omega,
-                                                         f[SET::R + I], f[SET::R + SET::P + I]), ...);
+// Relaxation of every population of a node of a compiled set (Eq. nm.8 with
+// feq = f0 + tau F, Eq. nm.2-nm.4), in place on the register values: the
+// polynomial form with the force, the per-pair form without it.
+template <class SET, int N, typename S, typename C>
+__device__ __forceinline__ void relax_ct(const KParams<C>& k, const CellCoef<C>& q, C* f) {
+    constexpr bool H = Storage<S>::scaled;
+    if (k.force) {
+        const PolyCoef<C> pc = poly_coef<N, true, H, C>(q, H ? k.om_s : C(1));
+        if constexpr (SET::R) {
+            if constexpr (H) f[0] = fma(k.one_m_omega, f[0], pc.c00);
+            else f[0] = fma(k.one_m_omega, f[0], k.omw_rest * q.a0);
+        }
+        poly_relax_all<SET, N, H, C>(k, pc, f, std::make_integer_sequence<int, SET::P>{});
+    } else {
+        if constexpr (SET::R) {
+            if constexpr (H) f[0] = fma(k.one_m_omega, f[0], mul_rn(k.om_s, q.a0));
+            else f[0] = fma(k.one_m_omega, f[0], k.omw_rest * q.a0);
+        }
+        relax_free_all<SET, N, H, C>(k, q, f, std::make_integer_sequence<int, SET::P>{});
+    }
+}
+
+// Stored values of a node's post-collision register values.  16-bit storage
+// rounds stochastically, two values per conversion: the rest value with a
+// zero partner, then each +-e pair, with the random bits r0 + (p + 1) phi
+// (r0 the node's hash, phi = 0x9e3779b9) -- a function of (node, step,
+// pair) only, so every kernel that packs a node this way stores its bits.
+template <class SET, typename S, typename C>
+__device__ __forceinline__ void pack_ct(const C* f, unsigned r0, S* out) {
+    constexpr int R = SET::R, P = SET::P, V = R + 2 * P;
+    if constexpr (Storage<S>::scaled) {
+        if constexpr (R) {
+            S zero;
+            Storage<S>::sr2(f[0], 0.f, r0, out[0], zero);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+            Storage<S>::sr2(f[R + p], f[R + P + p], r0 + unsigned(p + 1) * 0x9e3779b9u, out[R + p],
+                            out[R + P + p]);
+    } else {
+#pragma unroll
+        for (int a = 0; a < V; ++a) out[a] = S(f[a]);
+    }
 }
 
 // Middle path of a tile whose rows all lie at least max|e_y| rows from both
@@ -519,7 +811,7 @@ __device__ __forceinline__ void pull_rows(const KParams<C>& k, const PTR& sp, in
 #pragma unroll
     for (int a = 0; a < V; ++a) {
         const int i = cell + k.dx[a] + (x < k.sx[a] ? k.Nx : 0);
-        f[a] = ld_pop<S, C>(k, static_cast<const S*>(sp[a])[i], a);
+        f[a] = ld_val<S, C>(static_cast<const S*>(sp[a])[i]);
     }
 }
 
@@ -546,12 +838,12 @@ __device__ __forceinline__ C pull_col(const KParams<C>& k, const PTR& sp, int ce
     } else {
         i = cell + (x < Nx + EX ? 0 : -Nx);
     }
-    return ld_pop<S, C>(k, ld_stream(static_cast<const S*>(sp[A]) + i), A);
+    return ld_val<S, C>(ld_stream(static_cast<const S*>(sp[A]) + i));
 }
 
 template <class SET, typename S, typename C, int A, class PTR>
 __device__ __forceinline__ C pull_col1(const KParams<C>& k, const PTR& sp, int cell) {
-    return ld_pop<S, C>(k, ld_stream(static_cast<const S*>(sp[A]) + cell + plane_ex<SET>(A)), A);
+    return ld_val<S, C>(ld_stream(static_cast<const S*>(sp[A]) + cell + plane_ex<SET>(A)));
 }
 
 template <class SET, typename S, typename C, class PTR, int... I>
@@ -601,7 +893,7 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
     C f[V];
     if (fast) {
 #pragma unroll
-        for (int a = 0; a < V; ++a) f[a] = ld_pop<S, C>(k, ld_stream(static_cast<const S*>(k.srcf[a]) + cell), a);
+        for (int a = 0; a < V; ++a) f[a] = ld_val<S, C>(ld_stream(static_cast<const S*>(k.srcf[a]) + cell));
     } else if (rows) {
         if (cell >= k.ncell) return;
         pull_rows_any<SET, S, C>(k, k.srcf, cell, f);
@@ -615,17 +907,14 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
         else
             pull_wall_ct<SET, S, C>(k, src, x, y, f, std::make_integer_sequence<int, V>{});
     }
-    C drho = R ? f[0] : C(0), Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
-    moments_ct<SET, C>(f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, P>{});
+    C drho, Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
+    moments_ct<SET, S, C>(k, f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, P>{});
     const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, Kxy, Kyy);
-    if (R) f[0] = fma(k.one_m_omega, f[0], k.omw_rest * q.a0);
-    if (k.force)
-        relax_ct<SET, N, true, C>(k, q, f, std::make_integer_sequence<int, P>{});
-    else
-        relax_ct<SET, N, false, C>(k, q, f, std::make_integer_sequence<int, P>{});
-    unsigned rs = sr_seed<S, C>(k.seed, cell);
+    relax_ct<SET, N, S, C>(k, q, f);
+    S out[V];
+    pack_ct<SET, S, C>(f, sr_seed<S, C>(k.seed, cell), out);
 #pragma unroll
-    for (int a = 0; a < V; ++a) static_cast<S*>(k.dstp[a])[cell] = st_pop<S, C>(k, f[a], a, rs);
+    for (int a = 0; a < V; ++a) static_cast<S*>(k.dstp[a])[cell] = out[a];
     emit_moments<C>(k, q, cell, b);
     flag_density<C>(q, b.status);
 }

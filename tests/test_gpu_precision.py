@@ -2,15 +2,16 @@
 
 Force-driven channel D2V16, N = 3, Nx = 1 x Ny = 64, Ma ~ 1e-3, Kn
 log-spaced over [0.01, 1]: steady mass flow (Eq. pf.1) and slip velocity
-(Eq. defSlip) relative to the oracle's steady state.
+(Eq. defSlip) relative to the oracle's steady state, target 1e-4.
 
-Measured errors on GB300 (max over the 8 Kn points), from which the
-tolerances below take a margin:
-  fp32 storage:            mdot 5.2e-5, u_s 1.5e-5   -> 1e-4 (the stated target)
-  fp16 + stochastic round: mdot 2.3e-4, u_s 1.0e-3   -> 1e-3 / 3e-3
-  bf16 + stochastic round: mdot 2.2e-3, u_s 3.6e-3   -> 5e-3 / 1e-2
-16-bit runs never reach max|du| < 1e-10 (rounding noise ~1e-7) and stop at
-the step cap; their steady state is a statistical one.
+fp32 storage is deterministic and converges (max|du| < 1e-10).  fp16 storage
+rounds every store stochastically, so its state never stops moving (rounding
+noise ~1e-7 per step): after 20,000 steps it is in a statistical steady
+state, and its observables are the time averages of the next 30,000 steps
+(lbm_average), which meet the same 1e-4 target.  bf16 storage (8 mantissa
+bits) is outside the 1e-4 target set: its averaged errors reach a few 1e-4
+(measured table in the design notes), so only its short-transient parity is
+tested here, at a tolerance set by its resolution.
 """
 import numpy as np
 import pytest
@@ -21,7 +22,7 @@ from lbm_inputs import kn_sweep, rho_field
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": (1e-4, 1e-4), "fp16": (1e-3, 3e-3), "bf16": (5e-3, 1e-2)}
+TOL = {"fp32": (1e-4, 1e-4), "fp16": (1e-4, 1e-4)}
 _REF = {}
 
 
@@ -57,19 +58,67 @@ def test_fp32_storage_kn_sweep(Kn):
     assert abs(u / u_o - 1) < TOL["fp32"][1]
 
 
-@pytest.mark.parametrize("precision", ["fp16", "bf16"])
-@pytest.mark.parametrize("Kn", [kn_sweep(8)[0], kn_sweep(8)[4], kn_sweep(8)[7]])
-def test_16bit_storage_kn_points(precision, Kn):
+def _gpu_averaged(Kn, precision, warm=20000, window=30000):
+    import paper_1510_08886_gb300 as lbm
+    e, w, c = lbm.dvm("D2V16")
+    s = lbm.Solver(e, w, c, 3, 1, 64, Kn, oracle.force_for_mach(Kn), precision=precision).init()
+    s.run_to_steady(1e-10, warm)          # scale refreshes; never converges in 16 bits
+    s.average(window)
+    assert s.status() == 0
+    return s.mass_flow(), s.slip_velocity()
+
+
+@pytest.mark.parametrize("Kn", list(kn_sweep(8)))
+def test_fp16_storage_kn_sweep_time_averaged(Kn):
     m_o, u_o = _oracle_steady(Kn)
-    m, u = _gpu_steady(Kn, precision, 50000)
-    assert abs(m / m_o - 1) < TOL[precision][0]
-    assert abs(u / u_o - 1) < TOL[precision][1]
+    m, u = _gpu_averaged(Kn, "fp16")
+    assert abs(m / m_o - 1) < TOL["fp16"][0]
+    assert abs(u / u_o - 1) < TOL["fp16"][1]
+
+
+def test_average_of_a_steady_state_is_the_state():
+    """lbm_average on a converged deterministic (fp64) solve: the samples
+    differ from the state by at most 70 steps of the tested per-step change,
+    so their mean does too; sampling every 7th of 70 steps."""
+    import paper_1510_08886_gb300 as lbm
+    e, w, c = lbm.dvm("D2V16")
+    Kn = 0.2
+    s = lbm.Solver(e, w, c, 3, 3, 32, Kn, oracle.force_for_mach(Kn), precision="fp64").init()
+    assert s.run_to_steady(1e-14, 100000)[0]
+    m0, u0 = s.mass_flow(), s.slip_velocity()
+    _, ux0, _ = s.moments()
+    s.average(70, every=7)
+    _, ux1, _ = s.moments()
+    assert np.max(np.abs(ux1 - ux0)) < 70 * 1e-14
+    scale = 70 * 1e-14 / np.max(np.abs(ux0))
+    assert abs(s.mass_flow() / m0 - 1) < scale and abs(s.slip_velocity() / u0 - 1) < 10 * scale
+
+
+def test_average_is_the_sample_mean():
+    """The averaged field equals the mean of the per-step snapshots of a
+    second, identical solve (same seeds: bitwise the same states)."""
+    import paper_1510_08886_gb300 as lbm
+    e, w, c = lbm.dvm("D2V33")
+    Kn, Nx, Ny = 0.1, 40, 24
+    g = oracle.force_for_mach(Kn, 1e-2)
+    rho = rho_field(Nx, Ny, seed=9)
+    a = lbm.Solver(e, w, c, 4, Nx, Ny, Kn, g, precision="fp16").init(rho).step(30)
+    b = lbm.Solver(e, w, c, 4, Nx, Ny, Kn, g, precision="fp16").init(rho).step(30)
+    a.average(12, every=3)
+    acc = np.zeros((Ny, Nx))
+    for _ in range(4):
+        b.step(3)
+        acc += b.moments()[1]
+    assert np.max(np.abs(a.moments()[1] - acc / 4)) < 1e-15 * np.max(np.abs(acc)) + 1e-18
+    assert np.array_equal(a.populations(), b.populations())
 
 
 @pytest.mark.parametrize("precision", ["fp16", "bf16"])
 def test_16bit_parity_after_steps(precision):
     """Short transient with a seeded density field: moments within the
-    16-bit storage resolution of the oracle."""
+    16-bit storage resolution of the oracle (rho: a few units of the
+    format's relative resolution 2^-11 / 2^-8 times the deviation scale;
+    u: relative to max|u|)."""
     import paper_1510_08886_gb300 as lbm
     Kn, Nx, Ny = 0.1, 300, 24
     g = oracle.force_for_mach(Kn, 1e-2)
