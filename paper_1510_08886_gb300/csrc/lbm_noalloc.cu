@@ -5,10 +5,15 @@
 // array instead of memory from cudaMalloc or a workspace.  The array exists
 // once per device that loads this library and is held until the process
 // exits.  Host code only ever sees a host-side stand-in for the array's name,
-// so the device address is looked up with cudaGetSymbolAddress, once per
-// device, with that device current, and handed to the kernels.
-#include <atomic>
+// so the device address is looked up with cudaGetSymbolAddress, with the
+// device current, and handed to the kernels.  The address belongs to the
+// device's current context: it is looked up once per device and again
+// whenever the context changes (after a cudaDeviceReset the module is loaded
+// anew and the array may move).
+#include <cuda.h>
+
 #include <cmath>
+#include <mutex>
 
 #include "lbm.h"
 
@@ -23,7 +28,41 @@ constexpr int kMaxDevices = 64;
 // Scratch shared by every call on a device: kMaxPartials doubles (32 KiB).
 static __device__ __align__(256) double g_noalloc_partial[kMaxPartials];
 
-std::atomic<double*> g_scratch[kMaxDevices];
+// Per device: the unique id of the context the address was looked up in
+// (a context handle can be reused after a reset; its id is not), and the
+// address.
+struct ScratchSlot {
+    unsigned long long ctx_id = 0;
+    double* ptr = nullptr;
+};
+ScratchSlot g_scratch[kMaxDevices];
+std::mutex g_scratch_mu;
+
+// cuCtxGetCurrent and cuCtxGetId through the runtime's driver entry points
+// (the library does not link the driver library itself).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+void* driver_fn(const char* name) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return p;
+}
+
+// Unique id of the calling thread's current context (0: none).
+int current_context_id(unsigned long long* id) {
+    static const CtxGetCurrentFn get_ctx =
+        reinterpret_cast<CtxGetCurrentFn>(driver_fn("cuCtxGetCurrent"));
+    static const CtxGetIdFn get_id = reinterpret_cast<CtxGetIdFn>(driver_fn("cuCtxGetId"));
+    if (!get_ctx || !get_id) return LBM_ECUDA;
+    CUcontext ctx = nullptr;
+    if (get_ctx(&ctx) != CUDA_SUCCESS) return LBM_ECUDA;
+    *id = 0;
+    if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return LBM_ECUDA;
+    return LBM_OK;
+}
 
 __device__ double block_sum_na(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -83,20 +122,25 @@ k_noalloc_final(const double* __restrict__ partial, int nblk, const double* __re
 }
 
 // Device address of the scratch array on the current device, looked up on
-// the first call per device.
+// the first call per device and again when the device's context has changed.
 int scratch_for_current_device(double** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return LBM_ECUDA;
     if (dev >= kMaxDevices) return LBM_ENOTSUP;
-    double* p = g_scratch[dev].load(std::memory_order_acquire);
-    if (!p) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    ScratchSlot& slot = g_scratch[dev];
+    unsigned long long id = 0;
+    if (current_context_id(&id)) return LBM_ECUDA;
+    if (id == 0 || id != slot.ctx_id || !slot.ptr) {
+        // the lookup also creates the device's primary context if there is none yet
         void* addr = nullptr;
         if (cudaGetSymbolAddress(&addr, g_noalloc_partial) != cudaSuccess || !addr)
             return LBM_ECUDA;
-        p = static_cast<double*>(addr);
-        g_scratch[dev].store(p, std::memory_order_release);
+        if (current_context_id(&id) || id == 0) return LBM_ECUDA;
+        slot.ctx_id = id;
+        slot.ptr = static_cast<double*>(addr);
     }
-    *out = p;
+    *out = slot.ptr;
     return LBM_OK;
 }
 
@@ -109,6 +153,9 @@ extern "C" int lbm_observables_noalloc(const double* ux_device, int Nx, int Ny, 
         return LBM_EINVAL;
     const long long n = (long long)Nx * Ny;
     if (n > kMaxNodes) return LBM_EINVAL;
+    // an error already pending on this thread belongs to earlier work: leave
+    // it for its owner (cudaPeekAtLastError does not clear it) and refuse
+    if (cudaPeekAtLastError() != cudaSuccess) return LBM_ECUDA;
     double* scratch = nullptr;
     const int rc = scratch_for_current_device(&scratch);
     if (rc) return rc;
@@ -116,7 +163,15 @@ extern "C" int lbm_observables_noalloc(const double* ux_device, int Nx, int Ny, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const double tau = std::sqrt(2.0 / M_PI) * Kn;   // Eq. nm.13, as in lbm_create
     k_noalloc_partial<<<nblk, kThreads, 0, st>>>(ux_device, n, scratch);
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        cudaGetLastError();   // this call's own launch error: report it and clear it
+        return LBM_ECUDA;
+    }
     k_noalloc_final<<<1, kThreads, 0, st>>>(scratch, nblk, ux_device, Nx, Ny, tau, force, Kn,
                                             out_device);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ECUDA;
+    }
+    return LBM_OK;
 }
