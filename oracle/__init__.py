@@ -25,10 +25,10 @@ from . import dvm  # noqa: F401  (re-export)
 _lib = None
 
 
-def _load():
+def _load(path=None):
     global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(_build.build())
+    if _lib is None or path is not None:
+        lib = ctypes.CDLL(path or _build.build())
         dp = ctypes.POINTER(ctypes.c_double)
         P = ctypes.POINTER(_Params)
         lib.oracle_run.argtypes = [P, dp, dp, ctypes.c_long]
@@ -42,8 +42,21 @@ def _load():
         lib.oracle_force.argtypes = [P, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, dp, dp]
         lib.oracle_force.restype = None
+        lib.oracle_threads.argtypes = [ctypes.c_int]
+        lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
+
+
+def use_openmp(threads):
+    """Switch this process to the OpenMP build of the oracle (the CPU
+    baseline's timing on all host cores; the per-node arithmetic is the
+    serial build's) with `threads` threads.  Returns the thread count in use,
+    or None when no OpenMP build is available (the serial build stays)."""
+    path = _build.build_omp()
+    if path is None:
+        return None
+    return _load(path).oracle_threads(int(threads))
 
 
 class _Params(ctypes.Structure):

@@ -146,19 +146,29 @@ static void collide_node(const oracle_params* p, const double* fin, double* fout
     }
 }
 
+/* Nodes are independent: the row loop may run in parallel (OpenMP build of
+ * the CPU baseline only; each node's arithmetic is the same either way). */
 int oracle_collide(const oracle_params* p, const double* f, double* fstar) {
     const int V = p->V;
-    double* fin = malloc(sizeof(double) * 4 * V);
-    if (!fin) return -1;
-    double *fout = fin + V, *f0 = fin + 2 * V, *F = fin + 3 * V;
-    for (int y = 0; y < p->Ny; ++y)
-        for (int x = 0; x < p->Nx; ++x) {
-            for (int a = 0; a < V; ++a) fin[a] = f[at(p, a, x, y)];
-            collide_node(p, fin, fout, f0, F);
-            for (int a = 0; a < V; ++a) fstar[at(p, a, x, y)] = fout[a];
+    int failed = 0;
+#pragma omp parallel reduction(| : failed)
+    {
+        double* fin = malloc(sizeof(double) * 4 * V);
+        if (!fin) {
+            failed = 1;
+        } else {
+            double *fout = fin + V, *f0 = fin + 2 * V, *F = fin + 3 * V;
+#pragma omp for schedule(static)
+            for (int y = 0; y < p->Ny; ++y)
+                for (int x = 0; x < p->Nx; ++x) {
+                    for (int a = 0; a < V; ++a) fin[a] = f[at(p, a, x, y)];
+                    collide_node(p, fin, fout, f0, F);
+                    for (int a = 0; a < V; ++a) fstar[at(p, a, x, y)] = fout[a];
+                }
+            free(fin);
         }
-    free(fin);
-    return 0;
+    }
+    return failed ? -1 : 0;
 }
 
 /* Alternative reading of the wall condition (wall_mode = 1): Eq. nm.14 sets
@@ -244,6 +254,7 @@ int oracle_stream(const oracle_params* p, const double* fstar, double* f) {
         if (p->ey[a] < 0) den_top += -p->ey[a] * p->w[a];
     }
 
+#pragma omp parallel for collapse(2) schedule(static)
     for (int a = 0; a < V; ++a)
         for (int y = 0; y < Ny; ++y)
             for (int x = 0; x < Nx; ++x) {
@@ -287,6 +298,21 @@ void oracle_moments(const oracle_params* p, const double* f, double* rho,
             uy[i] = (m1 + 0.5 * p->dt * r * p->gy) / r;
         }
 }
+
+/* Threads of the OpenMP build (the CPU-baseline timing); returns the count
+ * in use, 1 in the serial build. */
+#ifdef _OPENMP
+#include <omp.h>
+int oracle_threads(int n) {
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+}
+#else
+int oracle_threads(int n) {
+    (void)n;
+    return 1;
+}
+#endif
 
 /* Single-node helpers exposed for the pins: equilibrium and force terms. */
 void oracle_equilibrium(const oracle_params* p, double rho, double ux, double uy,

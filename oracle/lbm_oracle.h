@@ -29,6 +29,8 @@ void oracle_moments(const oracle_params* p, const double* f, double* rho,
                     double* ux, double* uy);
 void oracle_equilibrium(const oracle_params* p, double rho, double ux,
                         double uy, double* f0);
+/* OpenMP build: set (n > 0) and return the thread count; serial build: 1. */
+int oracle_threads(int n);
 /* Pi4 = {Pi_xx, Pi_xy, Pi_yx, Pi_yy} */
 void oracle_force(const oracle_params* p, double rho, double ux, double uy,
                   const double* Pi4, double* F);
