@@ -276,10 +276,11 @@ int lbm_set_state(lbm_solver* s, const void* host, size_t bytes);
  * is admitted only if its footprint (lbm_engine_solve_bytes) fits.
  * Supported: the velocity sets with compiled kernels (the paper's D2V16,
  * D2V32, D2V33 and the (x, z) marginals of D3V107, D3V96, D3V112;
- * LBM_ENOTSUP otherwise), storage LBM_FP32, LBM_FP16 or LBM_BF16 (the 16-bit
- * scale S stays 2^-6 in the engine).  Each solve's arithmetic is the one of
- * lbm_step, so a solve's results do not depend on which other solves share
- * the engine.  Not thread-safe. */
+ * LBM_ENOTSUP otherwise), storage LBM_FP64 (fp64 arithmetic), LBM_FP32,
+ * LBM_FP16 or LBM_BF16 (fp32 arithmetic; the 16-bit scale S stays 2^-6 in the
+ * engine).  Each solve's arithmetic is the one of lbm_step's compiled-set
+ * kernel, so a solve's results do not depend on which other solves share the
+ * engine.  Not thread-safe. */
 typedef struct lbm_engine lbm_engine;
 
 /* Device bytes one solve occupies in an engine arena. */

@@ -4,7 +4,9 @@
 // (bundles of channels small enough to run a whole chunk in shared memory,
 // tiles of the others), CUDA-graph capture of a chunk of time steps plus the
 // per-solve reductions, and an autotuner of the persistent grid size and the
-// tiles taken per grab.
+// tiles taken per grab.  Storage fp64 (fp64 arithmetic), fp32, fp16 or bf16
+// (fp32 arithmetic); the device slot records are EngineSolve<double> for fp64
+// and EngineSolve<float> otherwise.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -21,17 +23,23 @@ namespace lbm {
 cudaError_t engine_step_fp32(int set_id, int N, const EngineLaunch& L, cudaStream_t st);
 cudaError_t engine_step_half(int set_id, int N, const EngineLaunch& L, cudaStream_t st);
 cudaError_t engine_step_bf16(int set_id, int N, const EngineLaunch& L, cudaStream_t st);
+cudaError_t engine_step_fp64(int set_id, int N, const EngineLaunch& L, cudaStream_t st);
 int engine_occupancy_fp32(int set_id, int N);
 int engine_occupancy_half(int set_id, int N);
 int engine_occupancy_bf16(int set_id, int N);
+int engine_occupancy_fp64(int set_id, int N);
 cudaError_t engine_resident_fp32(int set_id, int N, const ResidentLaunch& L, cudaStream_t st);
 cudaError_t engine_resident_half(int set_id, int N, const ResidentLaunch& L, cudaStream_t st);
 cudaError_t engine_resident_bf16(int set_id, int N, const ResidentLaunch& L, cudaStream_t st);
+cudaError_t engine_resident_fp64(int set_id, int N, const ResidentLaunch& L, cudaStream_t st);
 int engine_resident_attr_fp32(int set_id, int N, size_t smem);
 int engine_resident_attr_half(int set_id, int N, size_t smem);
 int engine_resident_attr_bf16(int set_id, int N, size_t smem);
+int engine_resident_attr_fp64(int set_id, int N, size_t smem);
 cudaError_t engine_reduce(const void* solves, const int* active, double* out, int nslots,
                           cudaStream_t st);
+cudaError_t engine_reduce_fp64(const void* solves, const int* active, double* out, int nslots,
+                               cudaStream_t st);
 cudaError_t engine_advance(unsigned int* seed, unsigned int by, cudaStream_t st);
 }  // namespace lbm
 
@@ -119,6 +127,12 @@ struct EngSlot {
     size_t off = 0, bytes = 0;
     long steps = 0;
     int group = -1;
+    // device buffers of the solve (also in its device record)
+    void* f[2] = {nullptr, nullptr};
+    double *rho = nullptr, *ux = nullptr, *uy = nullptr, *prev = nullptr;
+    unsigned* status = nullptr;
+    int phase = 0;
+    double tau = 0, g = 0;
 };
 
 __global__ void k_fill_ones(double* p, int n) {
@@ -141,7 +155,8 @@ struct lbm_engine {
     Arena arena;                               // over [ctrl, bytes)
     int max_slots = 0;
     size_t tile_cap = 0;
-    lbm::EngineSolve<float>* d_solves = nullptr;
+    void* d_solves = nullptr;                  // EngineSolve<double or float>[max_slots]
+    size_t rec_bytes = 0;                      // bytes of one record
     int* d_active = nullptr;
     double* d_results = nullptr;
     unsigned* d_status = nullptr;
@@ -150,7 +165,7 @@ struct lbm_engine {
     unsigned* d_seed = nullptr;
     lbm::EngineTile* d_tiles = nullptr;
     std::vector<EngSlot> slots;
-    std::vector<lbm::EngineSolve<float>> h_solves;
+    std::vector<unsigned char> h_rec;          // host copies of the records
     std::vector<int> h_active;
     std::vector<double> h_results;
     // asynchronous chunks: per outstanding launch, its results copied in
@@ -188,6 +203,7 @@ int occupancy(const lbm_engine* e, int group) {
     const int set = group / 3, N = group % 3 + 2;
     const int b = e->precision == LBM_FP16   ? lbm::engine_occupancy_half(set, N)
                   : e->precision == LBM_BF16 ? lbm::engine_occupancy_bf16(set, N)
+                  : e->precision == LBM_FP64 ? lbm::engine_occupancy_fp64(set, N)
                                              : lbm::engine_occupancy_fp32(set, N);
     return std::max(1, b);
 }
@@ -199,6 +215,7 @@ int res_occupancy(lbm_engine* e, int group) {
         e->res_occ[group] =
             e->precision == LBM_FP16   ? lbm::engine_resident_attr_half(set, N, e->res_smem)
             : e->precision == LBM_BF16 ? lbm::engine_resident_attr_bf16(set, N, e->res_smem)
+            : e->precision == LBM_FP64 ? lbm::engine_resident_attr_fp64(set, N, e->res_smem)
                                        : lbm::engine_resident_attr_fp32(set, N, e->res_smem);
     }
     return e->res_occ[group];
@@ -412,6 +429,7 @@ int enqueue_chunk(lbm_engine* e) {
             const int set = w.g / 3, N = w.g % 3 + 2;
             err = e->precision == LBM_FP16   ? lbm::engine_resident_half(set, N, L, rs)
                   : e->precision == LBM_BF16 ? lbm::engine_resident_bf16(set, N, L, rs)
+                  : e->precision == LBM_FP64 ? lbm::engine_resident_fp64(set, N, L, rs)
                                              : lbm::engine_resident_fp32(set, N, L, rs);
             if (err != cudaSuccess) return cuda_rc(err);
         }
@@ -434,6 +452,7 @@ int enqueue_chunk(lbm_engine* e) {
             const int set = w.g / 3, N = w.g % 3 + 2;
             err = e->precision == LBM_FP16   ? lbm::engine_step_half(set, N, L, ts)
                   : e->precision == LBM_BF16 ? lbm::engine_step_bf16(set, N, L, ts)
+                  : e->precision == LBM_FP64 ? lbm::engine_step_fp64(set, N, L, ts)
                                              : lbm::engine_step_fp32(set, N, L, ts);
             if (err != cudaSuccess) return cuda_rc(err);
         }
@@ -443,7 +462,9 @@ int enqueue_chunk(lbm_engine* e) {
         if (err == cudaSuccess) err = cudaStreamWaitEvent(e->stream, e->ev_join[l - 1], 0);
         if (err != cudaSuccess) return cuda_rc(err);
     }
-    err = lbm::engine_reduce(e->d_solves, e->d_active, e->d_results, e->max_slots, e->stream);
+    err = e->precision == LBM_FP64
+              ? lbm::engine_reduce_fp64(e->d_solves, e->d_active, e->d_results, e->max_slots, e->stream)
+              : lbm::engine_reduce(e->d_solves, e->d_active, e->d_results, e->max_slots, e->stream);
     if (err == cudaSuccess) err = lbm::engine_advance(e->d_seed, unsigned(e->K), e->stream);
     return cuda_rc(err);
 }
@@ -493,13 +514,68 @@ int fetch_results(lbm_engine* e, double* out) {
     return LBM_OK;
 }
 
+// Device record of a slot (compute type C), its initial state fbar = rho w,
+// first relaxation and moments (the single-solve init kernel).
+template <typename C>
+cudaError_t upload_and_init(lbm_engine* e, int slot, double Kn, const double* rho_host) {
+    const EngSlot& sl = e->slots[slot];
+    const lbm::SolveSpec& spec = sl.spec;
+    auto& h = *reinterpret_cast<lbm::EngineSolve<C>*>(e->h_rec.data() + size_t(slot) * e->rec_bytes);
+    std::memset(&h, 0, sizeof(h));
+    lbm::fill_params(spec, h.k);
+    h.f[0] = sl.f[0];
+    h.f[1] = sl.f[1];
+    h.rho = sl.rho;
+    h.ux = sl.ux;
+    h.uy = sl.uy;
+    h.prev = sl.prev;
+    h.status = sl.status;
+    h.phase = sl.phase;
+    h.kn = Kn;
+    h.tau = sl.tau;
+    h.g = sl.g;
+    lbm::DevBufs db{};
+    db.f[0] = h.f[0];
+    db.f[1] = h.f[1];
+    db.rho = h.rho;
+    db.ux = h.ux;
+    db.uy = h.uy;
+    db.prev_ux = h.prev;
+    db.status = h.status;
+    const int n = spec.Nx * spec.Ny;
+    cudaError_t err = cudaMemcpyAsync(static_cast<char*>(e->d_solves) + size_t(slot) * e->rec_bytes,
+                                      &h, sizeof(h), cudaMemcpyHostToDevice, e->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(h.status, 0, sizeof(unsigned), e->stream);
+    if (err == cudaSuccess) {
+        if (rho_host) {
+            err = cudaMemcpyAsync(h.prev, rho_host, size_t(n) * 8, cudaMemcpyHostToDevice, e->stream);
+        } else {
+            k_fill_ones<<<(n + 255) / 256, 256, 0, e->stream>>>(h.prev, n);
+            err = cudaGetLastError();
+        }
+    }
+    if (err == cudaSuccess) {
+        lbm::KParams<C> k = h.k;
+        k.emit = 1;
+        k.seed = 0u;
+        if constexpr (sizeof(C) == 8)
+            err = lbm::launch_init_fp64(k, spec.N, h.prev, h.f[0], db, e->stream);
+        else
+            err = is16(e->precision)
+                      ? lbm::launch_init_fp16(k, spec.N, e->precision == LBM_BF16, h.prev, h.f[0], db,
+                                              e->stream)
+                      : lbm::launch_init_fp32(k, spec.N, h.prev, h.f[0], db, e->stream);
+    }
+    return err;
+}
+
 }  // namespace
 
 extern "C" {
 
 int lbm_engine_solve_bytes(const lbm_dvm* dvm, int Nx, int Ny, int precision, size_t* bytes) {
     if (!dvm || !bytes || Nx < 1 || Ny < 1 || dvm->V < 1 || dvm->V > LBM_MAX_V) return LBM_EINVAL;
-    if (precision != LBM_FP32 && !is16(precision)) return LBM_EINVAL;
+    if (precision != LBM_FP32 && precision != LBM_FP64 && !is16(precision)) return LBM_EINVAL;
     *bytes = slot_layout(dvm->V, size_t(Nx) * Ny, lbm::elem_bytes(precision)).total;
     return LBM_OK;
 }
@@ -508,7 +584,8 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
                       lbm_engine** out) {
     if (!out) return LBM_EINVAL;
     *out = nullptr;
-    if ((precision != LBM_FP32 && !is16(precision)) || max_solves < 1 || max_solves > 65536)
+    if ((precision != LBM_FP32 && precision != LBM_FP64 && !is16(precision)) || max_solves < 1 ||
+        max_solves > 65536)
         return LBM_EINVAL;
     if (arena && (reinterpret_cast<uintptr_t>(arena) & 255)) return LBM_EINVAL;
     lbm_engine* e = new (std::nothrow) lbm_engine();
@@ -522,7 +599,9 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
     e->tile_cap = max_cells / lbm::kBlock + size_t(max_solves) + 1;
     size_t off = 0;
     auto take = [&](size_t n) { size_t o = off; off = al256(off + n); return o; };
-    const size_t o_solves = take(sizeof(lbm::EngineSolve<float>) * max_solves);
+    e->rec_bytes = precision == LBM_FP64 ? sizeof(lbm::EngineSolve<double>)
+                                         : sizeof(lbm::EngineSolve<float>);
+    const size_t o_solves = take(e->rec_bytes * max_solves);
     const size_t o_active = take(sizeof(int) * max_solves);
     const size_t o_results = take(sizeof(double) * 4 * max_solves);
     const size_t o_status = take(sizeof(unsigned) * max_solves);
@@ -544,7 +623,7 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
     }
     e->bytes = arena_bytes;
     e->arena.reset(arena_bytes - e->ctrl);
-    e->d_solves = reinterpret_cast<lbm::EngineSolve<float>*>(e->base + o_solves);
+    e->d_solves = e->base + o_solves;
     e->d_active = reinterpret_cast<int*>(e->base + o_active);
     e->d_results = reinterpret_cast<double*>(e->base + o_results);
     e->d_status = reinterpret_cast<unsigned*>(e->base + o_status);
@@ -558,7 +637,7 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
     e->d_seed = reinterpret_cast<unsigned*>(e->base + o_seed);
     e->d_tiles = reinterpret_cast<lbm::EngineTile*>(e->base + o_tiles);
     e->slots.resize(max_solves);
-    e->h_solves.resize(max_solves);
+    e->h_rec.assign(e->rec_bytes * size_t(max_solves), 0);
     e->h_active.assign(max_solves, 0);
     e->h_results.assign(4 * size_t(max_solves), 0.0);
     if (cudaMallocHost(&e->pinned, sizeof(double) * 8 * size_t(max_solves)) != cudaSuccess) {
@@ -638,50 +717,18 @@ int lbm_engine_add(lbm_engine* e, const lbm_dvm* dvm, int order, int Nx, int Ny,
     sl.bytes = L.total;
     sl.steps = 0;
     sl.group = group_of(spec);
-    lbm::EngineSolve<float>& h = e->h_solves[slot];
-    std::memset(&h, 0, sizeof(h));
-    lbm::fill_params(spec, h.k);
-    h.f[0] = b + L.f0;
-    h.f[1] = b + L.f1;
-    h.rho = reinterpret_cast<double*>(b + L.rho);
-    h.ux = reinterpret_cast<double*>(b + L.ux);
-    h.uy = reinterpret_cast<double*>(b + L.uy);
-    h.prev = reinterpret_cast<double*>(b + L.prev);
-    h.status = e->d_status + slot;
-    h.phase = 0;
-    h.kn = Kn;
-    h.tau = spec.tau;
-    h.g = force;
-    // initial state fbar = rho w, first relaxation, moments (shared init kernel)
-    lbm::DevBufs db{};
-    db.f[0] = h.f[0];
-    db.f[1] = h.f[1];
-    db.rho = h.rho;
-    db.ux = h.ux;
-    db.uy = h.uy;
-    db.prev_ux = h.prev;
-    db.status = h.status;
-    const int n = Nx * Ny;
-    cudaError_t err = cudaMemcpyAsync(e->d_solves + slot, &h, sizeof(h), cudaMemcpyHostToDevice,
-                                      e->stream);
-    if (err == cudaSuccess) err = cudaMemsetAsync(h.status, 0, sizeof(unsigned), e->stream);
-    if (err == cudaSuccess) {
-        if (rho_host) {
-            err = cudaMemcpyAsync(h.prev, rho_host, size_t(n) * 8, cudaMemcpyHostToDevice, e->stream);
-        } else {
-            k_fill_ones<<<(n + 255) / 256, 256, 0, e->stream>>>(h.prev, n);
-            err = cudaGetLastError();
-        }
-    }
-    if (err == cudaSuccess) {
-        lbm::KParams<float> k = h.k;
-        k.emit = 1;
-        k.seed = 0u;
-        err = is16(e->precision)
-                  ? lbm::launch_init_fp16(k, spec.N, e->precision == LBM_BF16, h.prev, h.f[0], db,
-                                          e->stream)
-                  : lbm::launch_init_fp32(k, spec.N, h.prev, h.f[0], db, e->stream);
-    }
+    sl.f[0] = b + L.f0;
+    sl.f[1] = b + L.f1;
+    sl.rho = reinterpret_cast<double*>(b + L.rho);
+    sl.ux = reinterpret_cast<double*>(b + L.ux);
+    sl.uy = reinterpret_cast<double*>(b + L.uy);
+    sl.prev = reinterpret_cast<double*>(b + L.prev);
+    sl.status = e->d_status + slot;
+    sl.phase = 0;
+    sl.tau = spec.tau;
+    sl.g = force;
+    cudaError_t err = e->precision == LBM_FP64 ? upload_and_init<double>(e, slot, Kn, rho_host)
+                                               : upload_and_init<float>(e, slot, Kn, rho_host);
     e->h_active[slot] = 1;
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(e->d_active + slot, &e->h_active[slot], sizeof(int),
@@ -846,7 +893,7 @@ int lbm_engine_info(lbm_engine* e, int slot, long* steps, int* status) {
 
 int lbm_engine_moments(lbm_engine* e, int slot, double* rho, double* ux, double* uy) {
     if (!e || slot < 0 || slot >= e->max_slots || !e->slots[slot].used) return LBM_EINVAL;
-    const lbm::EngineSolve<float>& h = e->h_solves[slot];
+    const EngSlot& h = e->slots[slot];
     const size_t n = size_t(e->slots[slot].spec.Nx) * e->slots[slot].spec.Ny * 8;
     cudaError_t err = cudaSuccess;
     if (rho) err = cudaMemcpyAsync(rho, h.rho, n, cudaMemcpyDeviceToHost, e->stream);
@@ -883,7 +930,7 @@ int lbm_engine_get_state(lbm_engine* e, int slot, void* host, size_t bytes) {
     if (!e || !host || slot < 0 || slot >= e->max_slots || !e->slots[slot].used) return LBM_EINVAL;
     const EngSlot& sl = e->slots[slot];
     if (bytes < engine_state_bytes(sl)) return LBM_EINVAL;
-    const lbm::EngineSolve<float>& h = e->h_solves[slot];
+    const EngSlot& h = sl;
     const size_t n = size_t(sl.spec.Nx) * sl.spec.Ny, pb = size_t(sl.spec.V) * n * sl.spec.elem;
     EngineStateHeader hd{};
     std::memcpy(hd.magic, "LBMENG1", 8);
@@ -915,7 +962,7 @@ int lbm_engine_set_state(lbm_engine* e, int slot, const void* host, size_t bytes
     if (bytes < engine_state_bytes(sl)) return LBM_EINVAL;
     EngineStateHeader hd{};
     std::memcpy(&hd, host, sizeof(hd));
-    const lbm::EngineSolve<float>& h = e->h_solves[slot];
+    const EngSlot& h = sl;
     if (std::memcmp(hd.magic, "LBMENG1", 8) != 0 || hd.V != sl.spec.V || hd.Nx != sl.spec.Nx ||
         hd.Ny != sl.spec.Ny || hd.precision != e->precision || hd.N != sl.spec.N ||
         hd.set_id != sl.spec.set_id || hd.tau != h.tau || hd.g != h.g || hd.steps < 0)

@@ -189,7 +189,7 @@ RESIDENT_MIX = ([("D2V16", 3, 1, 2048, 0.02), ("D2V16", 3, 1, 4, 0.5), ("D2V33",
                 + [("D2V16", 3, 1, 16 + (i % 7), 0.01 * (1 + i)) for i in range(70)])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16", "fp64"])
 def test_resident_chunks_bitwise_equal_tiled(precision):
     """A whole chunk in shared memory (two-step in-place streaming, ghost
     rows at the walls) gives bitwise the per-step tiled kernel's states,
@@ -202,7 +202,7 @@ def test_resident_chunks_bitwise_equal_tiled(precision):
     # memory (the opt-in limit less 4 KiB, 256-byte granules) and the padded
     # node count is at most 4096 (include/lbm.h, lbm_engine_set_resident)
     cap = (torch.cuda.get_device_properties(0).shared_memory_per_block_optin - 4096) & ~255
-    es = {"fp32": 4, "fp16": 2, "bf16": 2}[precision]
+    es = {"fp32": 4, "fp16": 2, "bf16": 2, "fp64": 8}[precision]
     n_res = 0
     for name, N, Nx, Ny, Kn in RESIDENT_MIX:
         e, w, c = lbm.dvm(name)
@@ -314,3 +314,57 @@ def test_launch_wait_equals_run():
     assert np.array_equal(ra4[sa[0]], rb4[sb[0]])
     a.close()
     b.close()
+
+
+def test_fp64_engine_equals_single_solver():
+    """fp64 storage and arithmetic in the engine: every solve of the mix
+    (tiled and resident, all compiled velocity sets) matches the fp64
+    single-solve API within fp64 rounding, and alone equals in the mix bit
+    for bit."""
+    import paper_1510_08886_gb300 as lbm
+    mix = lbm.Engine("fp64", max_solves=16, arena_bytes=512 << 20, chunk=50)
+    slots = [_add(mix, s, seed=i + 1) for i, s in enumerate(MIX)]
+    assert sum(mix.paths()) == len(MIX) and mix.paths()[1] > 0
+    res_mix = mix.run(2).copy()
+    for i, spec in enumerate(MIX):
+        name, N, Nx, Ny, Kn = spec
+        alone = lbm.Engine("fp64", max_solves=2, arena_bytes=128 << 20, chunk=50)
+        s = _add(alone, spec, seed=i + 1)
+        res_alone = alone.run(2)
+        m_mix = mix.moments(slots[i], Nx, Ny)
+        for a, b in zip(m_mix, alone.moments(s, Nx, Ny)):
+            assert np.array_equal(a, b)
+        assert np.array_equal(res_mix[slots[i]], res_alone[s])
+        alone.close()
+        e, w, c = lbm.dvm(name)
+        single = lbm.Solver(e, w, c, N, Nx, Ny, Kn, oracle.force_for_mach(Kn, 1e-2),
+                            precision="fp64").init(rho_field(Nx, Ny, seed=i + 1)).step(100)
+        r, ux, uy = single.moments()
+        assert np.max(np.abs(ux - m_mix[1])) <= 1e-12 * np.max(np.abs(ux)), spec
+        assert np.max(np.abs(r - m_mix[0])) <= 1e-13, spec
+        assert abs(res_mix[slots[i], 1] / single.mass_flow() - 1) < 1e-12, spec
+    mix.close()
+
+
+def test_fp64_engine_stops_with_the_oracle():
+    """Config-1 channel to max|du| < 1e-10 in a busy fp64 engine: the same
+    stopping chunk as the oracle's run_to_steady and its mass flow to 1e-12."""
+    import paper_1510_08886_gb300 as lbm
+    eng = lbm.Engine("fp64", max_solves=8, arena_bytes=256 << 20)
+    for s in MIX[:3]:
+        _add(eng, s, seed=5)
+    e, w, c = lbm.dvm("D2V16")
+    Kn = 0.1
+    g = oracle.force_for_mach(Kn)
+    slot = eng.add(e, w, c, 3, 1, 64, Kn, g)
+    for _ in range(500):
+        res = eng.run(1)
+        if res[slot, 0] < 1e-10:
+            break
+    assert res[slot, 0] < 1e-10
+    ref = oracle.channel("D2V16", 3, 1, 64, Kn, g).init()
+    conv, steps, _ = ref.run_to_steady(1e-10, 50000)
+    assert conv and eng.info(slot)[0] == steps
+    assert abs(res[slot, 1] / ref.mass_flow() - 1) < 1e-12
+    assert abs(res[slot, 2] / ref.slip_velocity() - 1) < 1e-11
+    eng.close()
