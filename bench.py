@@ -347,76 +347,146 @@ def config1_section(lbm):
     return out
 
 
-def saturated_serving(lbm, items, sets):
-    """The stream with every request queued at once (capacity)."""
+def _serve(lbm, items, sets, lanes, realtime, route=None, chunk=100, max_solves=1024):
+    """Play the request list through engines of the given precisions
+    (lanes: name -> precision) and return (stats, requests by id)."""
     from paper_1510_08886_gb300.serving import ContinuousBatcher, requests_from_workload
+    engines = {name: lbm.Engine(prec, max_solves=max_solves,
+                                arena_bytes=(4 << 30) if prec == "fp64" else (2 << 30), chunk=chunk)
+               for name, prec in lanes.items()}
+    reqs = requests_from_workload(items)
+    b = ContinuousBatcher(engines if len(engines) > 1 else next(iter(engines.values())), sets,
+                          route=route)
+    st = b.serve(reqs, realtime=realtime)
+    for e in engines.values():
+        e.close()
+    return st, {r.rid: r for r in b.done}
+
+
+def _gate(served, ref, tol=1e-4):
+    """Relative mass-flow error of every served request against the fp64
+    reference at its own tolerance test; the gate holds when all are <= tol."""
+    errs = {rid: abs(r.mdot / ref[rid].mdot - 1) for rid, r in served.items()
+            if rid in ref and r.status == 0 and ref[rid].status == 0}
+    bad = [rid for rid, e in errs.items() if e > tol]
+    worst = sorted(bad, key=lambda rid: -errs[rid])[:5]
+    return errs, {"max": max(errs.values()) if errs else None,
+                  "median": float(np.median(list(errs.values()))) if errs else None,
+                  "requests": len(errs), "failing": len(bad), "gate_1e-4": not bad,
+                  "worst": [{"Ny": served[rid].Ny, "Kn": round(served[rid].Kn, 4),
+                             "tol": served[rid].tol, "steps": served[rid].steps,
+                             "steps_fp64": ref[rid].steps, "err": errs[rid],
+                             "lane": served[rid].lane} for rid in worst]}
+
+
+def _passing_stats(served, errs, wall, tol=1e-4):
+    ok = [r for rid, r in served.items() if rid in errs and errs[rid] <= tol]
+    lat = np.array([r.latency for r in ok]) if ok else np.array([math.nan])
+    return {"solves_per_s": len(ok) / wall, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "requests": len(ok)}
+
+
+def _equal_steps(lbm, served, sets, sample):
+    """fp64 engine advanced by exactly the served step count of each sampled
+    request: the precision error alone (no stopping-rule effect)."""
+    e, w, c = sets["D2V16"]
+    eng = lbm.Engine("fp64", max_solves=len(sample) + 1, arena_bytes=4 << 30, chunk=100)
+    slots = {}
+    for rid in sample:
+        r = served[rid]
+        slots[eng.add(e, w, c, r.order, r.Nx, r.Ny, r.Kn, r.force)] = rid
     out = {}
-    for chunk in (100, 200):
-        eng = lbm.Engine("fp32", max_solves=1024, arena_bytes=2 << 30, chunk=chunk)
-        st = ContinuousBatcher(eng, sets).serve(requests_from_workload(items), realtime=False)
-        eng.close()
-        out[f"chunk_{chunk}"] = {"solves_per_s": st.solves_per_s, "wall_s": st.wall_s,
-                                 "GLUPS": st.cell_steps / st.wall_s / 1e9,
-                                 "max_resident": st.max_resident}
+    steps = 0
+    while slots:
+        res = eng.run(1)
+        steps += 100
+        for sl in [sl for sl, rid in slots.items() if served[rid].steps <= steps]:
+            rid = slots.pop(sl)
+            out[rid] = abs(served[rid].mdot / float(res[sl, 1]) - 1)
+            eng.remove(sl)
+    eng.close()
     return out
 
 
 def serving_section(lbm, seconds, saturated_only=False):
     """Config-5 stream (Poisson 200/s, D2V16 N=3, Nx=1, Ny U{16..2048}, Kn
-    log-U[0.01,1], tol in {1e-6,1e-8}) for `seconds` of arrivals, served with
-    continuous batching (fp32 engine) vs the plain fp64 per-solve path."""
+    log-U[0.01,1], tol in {1e-6,1e-8}) for `seconds` of arrivals.
+
+    Reference: every request solved at its own tolerance by the fp64 engine
+    (fp64 storage and arithmetic, matching the single-solve fp64 path to
+    rounding; checked on the requests the plain path finishes).  Served:
+    continuous batching with precision routing (fp32 engine, and an fp64
+    engine for the requests whose stopping chunk fp32 could flip), in real
+    time and saturated; the same with fp32 only; an fp16-storage arm
+    (saturated).  Baseline: the plain per-solve fp64 path in real time.
+    Accuracy gate: relative mass-flow error <= 1e-4 against the reference,
+    per request; rates and latencies are also given over the passing
+    requests only."""
     from lbm_inputs import serving_workload
-    from paper_1510_08886_gb300.serving import ContinuousBatcher, requests_from_workload, serve_plain
+    from paper_1510_08886_gb300.serving import (PrecisionRouter, requests_from_workload,
+                                                serve_plain)
     items = serving_workload(duration_s=seconds)
     sets = {"D2V16": lbm.dvm("D2V16")}
+    router = PrecisionRouter(sets)
+    lanes = {"fp32": "fp32", "fp64": "fp64"}
+    out = {"stream": f"{len(items)} requests in {seconds:.0f} s (Poisson 200/s, seed 20151031)"}
+    ref_st, ref = _serve(lbm, items, sets, {"fp64": "fp64"}, realtime=False)
+    out["reference_fp64_engine_saturated"] = ref_st.as_dict()
+    sat_st, sat = _serve(lbm, items, sets, lanes, realtime=False, route=router)
+    errs_sat, gate_sat = _gate(sat, ref)
+    out["served_routed_saturated"] = {**sat_st.as_dict(), "accuracy": gate_sat,
+                                      "fp64_routed": sum(r.lane == "fp64" for r in sat.values()),
+                                      "passing": _passing_stats(sat, errs_sat, sat_st.wall_s)}
+    sat32_st, sat32 = _serve(lbm, items, sets, {"fp32": "fp32"}, realtime=False)
+    out["served_fp32_only_saturated"] = {**sat32_st.as_dict(), "accuracy": _gate(sat32, ref)[1]}
+    sat16_st, sat16 = _serve(lbm, items, sets, {"fp16": "fp16"}, realtime=False)
+    out["served_fp16_only_saturated"] = {**sat16_st.as_dict(), "accuracy": _gate(sat16, ref)[1]}
     if saturated_only:
-        return {"stream": f"{len(items)} requests in {seconds:.0f} s (Poisson 200/s, seed 20151031)",
-                "saturated": saturated_serving(lbm, items, sets)}
-    eng = lbm.Engine("fp32", max_solves=1024, arena_bytes=2 << 30, chunk=100)
-    b = ContinuousBatcher(eng, sets)
-    st = b.serve(requests_from_workload(items), realtime=True)
-    eng.close()
+        return out
+    st, served = _serve(lbm, items, sets, lanes, realtime=True, route=router)
+    errs, gate = _gate(served, ref)
+    out["served_routed_realtime"] = {**st.as_dict(), "accuracy": gate,
+                                     "fp64_routed": sum(r.lane == "fp64" for r in served.values()),
+                                     "passing": _passing_stats(served, errs, st.wall_s)}
+    st32, served32 = _serve(lbm, items, sets, {"fp32": "fp32"}, realtime=True)
+    errs32, gate32 = _gate(served32, ref)
+    out["served_fp32_only_realtime"] = {**st32.as_dict(), "accuracy": gate32,
+                                        "passing": _passing_stats(served32, errs32, st32.wall_s)}
     e, w, c = sets["D2V16"]
 
     def make(r):
         return lbm.Solver(e, w, c, r.order, r.Nx, r.Ny, r.Kn, r.force, precision="fp64").init()
 
-    served = {r.rid: r for r in b.done}
     plain_reqs = requests_from_workload(items)
     plain = serve_plain(plain_reqs, make, realtime=True, time_limit=max(seconds, 1.0))
-    # accuracy of the served fp32 results against the fp64 path on the requests
-    # both paths finished (the fp64 GPU path matches the oracle to 1e-12)
-    both = [r for r in plain_reqs if not math.isnan(r.t_done) and r.rid in served and r.converged]
-    errs = [abs(served[r.rid].mdot / r.mdot - 1) for r in both]
-    errs_small = [abs(served[r.rid].mdot / r.mdot - 1) for r in both if r.Ny <= 512]
-    # precision alone: the fp64 path advanced by exactly the served step count
-    same = []
-    for r in both[:40]:
-        sv = served[r.rid]
-        s64 = make(r).step(sv.steps)
-        same.append((r.Ny, abs(sv.mdot / s64.mass_flow() - 1)))
-        s64.close()
-    # capacity: the same stream with every request queued at once
-    sat = saturated_serving(lbm, items, sets)
-    sat_best = max(v["solves_per_s"] for v in sat.values())
-    return {"stream": f"{len(items)} requests in {seconds:.0f} s (Poisson 200/s, seed 20151031)",
-            "served_fp32_continuous_batching": st.as_dict(),
-            "plain_fp64_per_solve": plain.as_dict(),
-            "solves_per_s_ratio": st.solves_per_s / max(plain.solves_per_s, 1e-12),
-            "served_saturated": sat,
-            "served_saturated_solves_per_s": sat_best,
-            "saturated_vs_plain": sat_best / max(plain.solves_per_s, 1e-12),
-            "mdot_rel_err_fp32_vs_fp64": {"max": max(errs) if errs else None,
-                                          "median": float(np.median(errs)) if errs else None,
-                                          "requests": len(errs),
-                                          "max_Ny_le_512": max(errs_small) if errs_small else None,
-                                          "requests_Ny_le_512": len(errs_small),
-                                          "note": "each path stops at its own tolerance test"},
-            "mdot_rel_err_fp32_vs_fp64_same_steps": {
-                "max": max(e for _, e in same) if same else None,
-                "median": float(np.median([e for _, e in same])) if same else None,
-                "max_Ny_le_512": max([e for n, e in same if n <= 512], default=None),
-                "requests": len(same)}}
+    done = [r for r in plain_reqs if not math.isnan(r.t_done) and r.status == 0]
+    out["plain_fp64_per_solve"] = plain.as_dict()
+    out["plain_vs_fp64_engine_max_rel"] = max(
+        (abs(r.mdot / ref[r.rid].mdot - 1) for r in done if r.rid in ref), default=None)
+    out["plain_vs_fp64_engine_same_steps"] = sum(r.steps == ref[r.rid].steps for r in done
+                                                 if r.rid in ref)
+    out["plain_completed"] = len(done)
+    # precision alone, stratified over Ny and Kn, on fp32-served requests
+    fp32_served = [r for r in served.values() if r.lane == "fp32" and r.status == 0]
+    strata = {}
+    for r in fp32_served:
+        key = (min(3, r.Ny // 512), 0 if r.Kn < 0.1 else 1)
+        strata.setdefault(key, []).append(r)
+    sample = []
+    for key, rs in sorted(strata.items()):
+        rs.sort(key=lambda r: (-r.Ny, r.Kn))
+        sample += [r.rid for r in rs[:3]]
+    eq = _equal_steps(lbm, served, sets, sample)
+    out["fp32_equal_steps_precision"] = {
+        "max": max(eq.values()) if eq else None, "requests": len(eq),
+        "strata": {f"Ny{k[0] * 512}-{k[0] * 512 + 511}_Kn{'<' if k[1] == 0 else '>='}0.1":
+                   len(v) for k, v in sorted(strata.items())}}
+    p = out["plain_fp64_per_solve"]["solves_per_s"]
+    out["solves_per_s_ratio_passing"] = out["served_routed_realtime"]["passing"]["solves_per_s"] / \
+        max(p, 1e-12)
+    out["saturated_passing_vs_plain"] = out["served_routed_saturated"]["passing"]["solves_per_s"] / \
+        max(p, 1e-12)
+    return out
 
 
 def run_reference(args):

@@ -10,6 +10,14 @@ than its tolerance is harvested (mass flow, slip velocity) and its memory
 freed for the queue.  Requests that arrive while others are running join at
 the next chunk boundary.
 
+Precision routing: the loop can drive several engines at once (each on its
+own stream, so their chunks overlap on the GPU) and send each request to one
+of them.  ``PrecisionRouter`` sends a request to fp64 storage when its
+stopping decision is at risk in fp32: the per-step change of u_x that the
+tolerance test compares is only known to ~2e-10 from fp32 populations, and a
+test that lands on the other side of the tolerance stops the solve one chunk
+earlier or later, which moves the reported mass flow by ~chunk x tol / u.
+
 ``serve_plain`` is the comparison path: the same requests solved one at a
 time with the single-solve fp64 API.
 """
@@ -40,6 +48,7 @@ class Request:
     du: float = math.nan
     converged: bool = False
     status: int = 0
+    lane: str = ""
 
     @property
     def force(self):
@@ -88,39 +97,112 @@ def _stats(done, t0, t1, max_resident, chunks, cell_steps):
     return st
 
 
-class ContinuousBatcher:
-    """Drive an engine (paper_1510_08886_gb300.Engine, or any object with
-    add/remove/run/chunk, and optionally launch/wait) with a request queue."""
+def relaxation_steps(r, c):
+    """Time constant, in steps, of the slowest (viscous) mode of a channel
+    request: l0^2 / (pi^2 nu) with nu = tau = sqrt(2/pi) Kn (Eq. nm.11, nm.13)
+    and dt = 1 / (Ny c), i.e. Ny c / (pi^2 tau)."""
+    tau = math.sqrt(2.0 / math.pi) * r.Kn
+    return r.Ny * c / (math.pi ** 2 * tau)
 
-    def __init__(self, engine, velocity_sets, max_steps=200000, clock=time.perf_counter):
+
+class PrecisionRouter:
+    """Send a request to fp64 storage when fp32 may flip its stopping chunk.
+
+    Near the stop the per-step change du decays by exp(-chunk / T) per
+    chunk (T = relaxation_steps); fp32 populations know du only to about
+    `du_noise` (measured ~2e-10 at Ma 1e-3), so the test du < tol lands on
+    the wrong side of a chunk boundary with probability about
+    (du_noise / tol) x T / chunk.  Requests above `risk` go to "fp64", the
+    others to "fp32"."""
+
+    def __init__(self, velocity_sets, chunk=100, du_noise=2e-10, risk=1e-3):
+        self.c = {name: float(v[2]) for name, v in velocity_sets.items()}
+        self.chunk, self.du_noise, self.risk = chunk, du_noise, risk
+
+    def flip_risk(self, r):
+        return self.du_noise / r.tol * relaxation_steps(r, self.c[r.dvm]) / self.chunk
+
+    def __call__(self, r):
+        return "fp64" if self.flip_risk(r) > self.risk else "fp32"
+
+
+class _Lane:
+    """One engine of the batcher with its resident solves and in-flight chunks."""
+
+    def __init__(self, engine):
         self.engine = engine
+        self.active = {}                   # slot -> Request
+        self.inflight = []                 # snapshots of launched, unharvested chunks
+        self.chunks = 0
+
+
+class ContinuousBatcher:
+    """Drive one engine (paper_1510_08886_gb300.Engine, or any object with
+    add/remove/run/chunk, and optionally launch/wait), or several engines
+    keyed by name with `route(request) -> name`, with a request queue."""
+
+    def __init__(self, engine, velocity_sets, max_steps=200000, clock=time.perf_counter,
+                 route=None):
+        engines = engine if isinstance(engine, dict) else {"main": engine}
+        self.lanes = {k: _Lane(e) for k, e in engines.items()}
+        self.route = route if route is not None else (lambda r: next(iter(self.lanes)))
         self.sets = velocity_sets          # name -> (e, w, c)
         self.max_steps = max_steps
         self.clock = clock
         self.queue = []
-        self.active = {}                   # slot -> Request
         self.done = []
-        self.chunks = 0
         self.cell_steps = 0.0
         self.max_resident = 0
-        self._inflight = []                # snapshots of launched, unharvested chunks
+
+    # single-engine views (the common case)
+    @property
+    def engine(self):
+        return next(iter(self.lanes.values())).engine
+
+    @property
+    def active(self):
+        out = {}
+        for lane in self.lanes.values():
+            out.update(lane.active)
+        return out if len(self.lanes) > 1 else next(iter(self.lanes.values())).active
+
+    @property
+    def chunks(self):
+        return sum(l.chunks for l in self.lanes.values())
+
+    def _busy(self):
+        return any(l.active or l.inflight for l in self.lanes.values())
 
     def submit(self, req):
         self.queue.append(req)
 
     def admit(self):
-        """First fit over the queue in arrival order.  A request the engine
-        rejects (unknown velocity set, invalid arguments) is answered at once
-        with its error code instead of stopping the server."""
+        """First fit over the queue in arrival order, each request into its
+        routed engine.  A request the engine rejects (unknown velocity set,
+        invalid arguments) is answered at once with its error code instead of
+        stopping the server."""
         still = []
-        cap = getattr(self.engine, "max_solves", None)
+        full = set()
         for i, r in enumerate(self.queue):
-            if cap is not None and len(self.active) >= cap:
-                still.extend(self.queue[i:])      # no free slot: the rest waits
+            if len(full) == len(self.lanes):
+                still.extend(self.queue[i:])      # every engine's slots taken: the rest waits
                 break
             try:
+                name = self.route(r)
+                lane = self.lanes[name]
+            except KeyError as err:
+                r.status = getattr(err, "code", -1)
+                r.t_admit = r.t_done = self.clock()
+                self.done.append(r)
+                continue
+            cap = getattr(lane.engine, "max_solves", None)
+            if cap is not None and len(lane.active) >= cap:
+                full.add(name)
+                still.append(r)                   # no free slot in that engine: waits
+                continue
+            try:
                 e, w, c = self.sets[r.dvm]
-                slot = self.engine.add(e, w, c, r.order, r.Nx, r.Ny, r.Kn, r.force)
+                slot = lane.engine.add(e, w, c, r.order, r.Nx, r.Ny, r.Kn, r.force)
             except (KeyError, ValueError, RuntimeError) as err:
                 r.status = getattr(err, "code", -1)
                 r.t_admit = r.t_done = self.clock()
@@ -130,25 +212,28 @@ class ContinuousBatcher:
                 still.append(r)
                 continue
             r.t_admit = self.clock()
-            self.active[slot] = r
+            r.lane = name
+            lane.active[slot] = r
         self.queue = still
-        self.max_resident = max(self.max_resident, len(self.active))
+        self.max_resident = max(self.max_resident,
+                                sum(len(l.active) for l in self.lanes.values()))
 
-    def _launch_snapshot(self):
-        """Count one chunk for every resident solve; return (slot, request,
-        steps after the chunk) for the harvest of that chunk's results."""
-        self.chunks += 1
-        self.cell_steps += sum(r.Nx * r.Ny for r in self.active.values()) * self.engine.chunk
+    def _launch_snapshot(self, lane):
+        """Count one chunk for every resident solve of a lane; return (slot,
+        request, steps after the chunk) for the harvest of that chunk."""
+        lane.chunks += 1
+        K = lane.engine.chunk
+        self.cell_steps += sum(r.Nx * r.Ny for r in lane.active.values()) * K
         snap = []
-        for slot, r in self.active.items():
-            r.steps += self.engine.chunk
+        for slot, r in lane.active.items():
+            r.steps += K
             snap.append((slot, r, r.steps))
         return snap
 
-    def _harvest(self, res, snap):
+    def _harvest(self, lane, res, snap):
         """Retire the solves of a finished chunk whose result meets their
         tolerance, ran out of steps or turned non-finite (du NaN or inf)."""
-        live = [(s, r, st) for s, r, st in snap if self.active.get(s) is r]
+        live = [(s, r, st) for s, r, st in snap if lane.active.get(s) is r]
         if not live:
             return 0
         now = self.clock()
@@ -167,33 +252,38 @@ class ContinuousBatcher:
             r.t_done = now
             finished.append(slot)
         for slot in finished:
-            self.engine.remove(slot)
-            self.done.append(self.active.pop(slot))
+            lane.engine.remove(slot)
+            self.done.append(lane.active.pop(slot))
         return len(finished)
 
     def step(self):
         """Admit, advance every resident solve by one chunk, harvest.
 
-        With an engine that can launch asynchronously (launch/wait), the
-        next chunk is queued before the previous one's results are
+        With engines that can launch asynchronously (launch/wait), every
+        lane's next chunk is queued before the previous one's results are
         processed, so the GPU runs while the host harvests and admits: a
         solve is harvested from the results of the chunk that met its
         tolerance (its reported steps are that chunk's), it has already
         been queued for one more chunk by then, and an admitted request
         joins one chunk later."""
         self.admit()
-        if not hasattr(self.engine, "launch"):
-            if not self.active:
-                return 0
-            res = self.engine.run(1)
-            return self._harvest(res, self._launch_snapshot())
-        if self.active:
-            self.engine.launch(1)
-            self._inflight.append(self._launch_snapshot())
-        if self._inflight and (len(self._inflight) == 2 or not self.active):
-            res = self.engine.wait()
-            return self._harvest(res, self._inflight.pop(0))
-        return 0
+        n = 0
+        for lane in self.lanes.values():
+            if not hasattr(lane.engine, "launch"):
+                if lane.active:
+                    res = lane.engine.run(1)
+                    n += self._harvest(lane, res, self._launch_snapshot(lane))
+                continue
+            if lane.active:
+                lane.engine.launch(1)
+                lane.inflight.append(self._launch_snapshot(lane))
+        for lane in self.lanes.values():
+            if not hasattr(lane.engine, "launch"):
+                continue
+            if lane.inflight and (len(lane.inflight) == 2 or not lane.active):
+                res = lane.engine.wait()
+                n += self._harvest(lane, res, lane.inflight.pop(0))
+        return n
 
     def serve(self, requests, realtime=True, time_limit=None):
         """Play a request stream (t_arrival relative to the start) and return
@@ -202,7 +292,7 @@ class ContinuousBatcher:
         pending = sorted(requests, key=lambda r: r.t_arrival)
         t0 = self.clock()
         i = 0
-        while i < len(pending) or self.queue or self.active or self._inflight:
+        while i < len(pending) or self.queue or self._busy():
             now = self.clock()
             if time_limit is not None and now - t0 > time_limit:
                 break
@@ -211,7 +301,7 @@ class ContinuousBatcher:
                 r.t_arrival = t0 + r.t_arrival if realtime else t0
                 self.submit(r)
                 i += 1
-            if not self.queue and not self.active and not self._inflight and i < len(pending):
+            if not self.queue and not self._busy() and i < len(pending):
                 time.sleep(max(0.0, min(0.01, pending[i].t_arrival - (self.clock() - t0))))
                 continue
             self.step()

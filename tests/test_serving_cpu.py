@@ -296,3 +296,40 @@ def test_pipelined_slot_reuse_and_failures():
             T = 10.0 * r.Ny * r.Kn
             assert 1e-3 * math.exp(-r.steps / T) < r.tol          # converged at its steps
             assert 1e-3 * math.exp(-(r.steps - 100) / T) >= r.tol  # not a chunk earlier
+
+
+def test_precision_router_risk_and_lanes():
+    """Two engines behind one loop: the router's flip risk
+    (du_noise / tol) x T / chunk with T = Ny c / (pi^2 tau) sends tight or
+    slowly relaxing requests to "fp64"; each request is admitted, advanced
+    and harvested in its own engine only, and every request completes."""
+    from paper_1510_08886_gb300.serving import PrecisionRouter, relaxation_steps
+    sets = {"D2V16": (None, None, 1.5)}
+    router = PrecisionRouter(sets, chunk=100, du_noise=2e-10, risk=1e-3)
+    r_fast = Request(0, 0.0, "D2V16", 3, 1, 16, 1.0, 1e-6)
+    r_slow = Request(1, 0.0, "D2V16", 3, 1, 2000, 0.01, 1e-6)
+    r_tight = Request(2, 0.0, "D2V16", 3, 1, 64, 0.1, 1e-8)
+    tau = math.sqrt(2 / math.pi) * 0.01
+    assert abs(relaxation_steps(r_slow, 1.5) - 2000 * 1.5 / (math.pi ** 2 * tau)) < 1e-9
+    assert router(r_fast) == "fp32" and router(r_slow) == "fp64" and router(r_tight) == "fp64"
+    assert abs(router.flip_risk(r_tight) / router.flip_risk(Request(3, 0.0, "D2V16", 3, 1, 64, 0.1,
+                                                                    1e-6)) - 100) < 1e-9
+    clk = FakeClock()
+    engines = {"fp32": FakeEngine(10 ** 6, 8, clock=clk), "fp64": FakeEngine(10 ** 6, 8, clock=clk)}
+    seen = {"fp32": set(), "fp64": set()}
+    for name, eng in engines.items():
+        orig = eng.add
+
+        def add(*a, _orig=orig, _name=name):
+            slot = _orig(*a)
+            seen[_name].add((a[5], a[6]))     # (Ny, Kn)
+            return slot
+        eng.add = add
+    reqs = [Request(i, 0.0, "D2V16", 3, 1, ny, kn, tol) for i, (ny, kn, tol) in
+            enumerate([(16, 1.0, 1e-6), (2000, 0.01, 1e-6), (64, 0.1, 1e-8), (32, 0.5, 1e-6)] * 5)]
+    b = ContinuousBatcher(engines, sets, clock=clk, route=router)
+    st = b.serve(reqs, realtime=False)
+    assert st.completed == len(reqs)
+    assert all(r.lane == router(r) for r in reqs)
+    assert seen["fp64"] == {(2000, 0.01), (64, 0.1)} and seen["fp32"] == {(16, 1.0), (32, 0.5)}
+    assert all(r.converged for r in reqs)
