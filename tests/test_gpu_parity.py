@@ -315,3 +315,62 @@ def test_knudsen_minimum_s3_not_s4_on_gpu():
     s4 = np.array([res[slots[("D3V96xz", k)], 1] for k in kns])
     assert 1 <= int(np.argmin(s3)) <= 3 and s3[-1] > 1.05 * s3.min()
     assert np.all(np.diff(s4) < 0)
+
+
+@pytest.mark.parametrize("name,Kn", [("D3V66xz", 0.4514), ("D3V112xz", 0.1), ("D3V112xz", 0.4514),
+                                     ("D3V112xz", 1.0), ("D3V77xz", 0.1), ("D3V77xz", 0.4514),
+                                     ("D3V77xz", 1.0)])
+def test_marginal_models_steady_state_fp64(name, Kn):
+    """(x, z) marginals of the S1 model with the smallest |sigma_zxx| (D3V66,
+    Sect. VI.A: mass flow near the DSMC 1.76 at Kn = 0.4514), the scattering
+    S4 model D3V112 and the augmented S3 model D3V77 (Sect. VI.B-C), run to
+    max|du| < 1e-11 on the GPU in fp64: the oracle's stopping step, mass flow
+    and slip velocity."""
+    g = oracle.force_for_mach(Kn)
+    s, ref, _ = _pair(name, 3, 1, 64, Kn, g, None)
+    conv, steps, _ = s.run_to_steady(1e-11, 100000)
+    conv_o, steps_o, _ = ref.run_to_steady(1e-11, 100000)
+    assert conv and conv_o and steps == steps_o
+    assert abs(s.mass_flow() / ref.mass_flow() - 1) < 1e-12
+    assert abs(s.slip_velocity() / ref.slip_velocity() - 1) < 1e-11
+    if name == "D3V66xz":
+        assert abs(s.mass_flow() / 1.76 - 1) < 0.03
+
+
+def test_marginal_s4_engine_kn_sweep_fp32():
+    """The D3V112 (x, z) marginal (a compiled set) in the fp32 engine at
+    three Kn: steady mass flow within 1e-4 of the fp64 oracle."""
+    import paper_1510_08886_gb300 as lbm
+    e, w, c = lbm.dvm("D3V112xz")
+    eng = lbm.Engine("fp32", max_solves=4, arena_bytes=64 << 20)
+    kns = (0.1, 0.4514, 1.0)
+    slots = [eng.add(e, w, c, 3, 1, 64, Kn, oracle.force_for_mach(Kn)) for Kn in kns]
+    live = dict(zip(slots, kns))
+    mdot = {}
+    for _ in range(1000):
+        res = eng.run(1)
+        for sl in [sl for sl in live if res[sl, 0] < 1e-10]:
+            mdot[live.pop(sl)] = float(res[sl, 1])
+            eng.remove(sl)
+        if not live:
+            break
+    assert not live
+    eng.close()
+    for Kn in kns:
+        ref = oracle.channel("D3V112xz", 3, 1, 64, Kn, oracle.force_for_mach(Kn)).init()
+        assert ref.run_to_steady(1e-10, 100000)[0]
+        assert abs(mdot[Kn] / ref.mass_flow() - 1) < 1e-4, Kn
+
+
+def test_long_horizon_mass_and_rest_state_fp64():
+    """50,000 forced fp64 steps with walls and a seeded density: total mass
+    constant to 1e-13 relative; g = 0 at rest: fbar = w over 10,000 steps."""
+    import paper_1510_08886_gb300 as lbm
+    e, w, c = lbm.dvm("D2V33")
+    rho = rho_field(16, 24, seed=7)
+    s = lbm.Solver(e, w, c, 4, 16, 24, 0.1, oracle.force_for_mach(0.1), precision="fp64").init(rho)
+    s.step(50000)
+    assert abs(s.moments()[0].sum() / rho.sum() - 1) < 1e-13
+    r = lbm.Solver(e, w, c, 4, 2, 16, 0.1, 0.0, precision="fp64").init().step(10000)
+    f = r.populations()
+    assert np.max(np.abs(f - np.asarray(w)[:, None, None])) < 1e-14

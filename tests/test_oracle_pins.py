@@ -227,16 +227,20 @@ def test_stream_matches_push_brute_force(name, N, Nx, Ny):
 
 @pytest.mark.parametrize("name,N", SETS[:4])
 def test_rest_state_is_fixed_point(name, N):
+    """g = 0 and fbar = w: the state stays put over 10,000 steps."""
     ch = _chan(name, N, Nx=2, Ny=16, g=0.0).init()
-    ch.step(500)
+    ch.step(10000)
     assert np.max(np.abs(ch.f - ch.w[:, None, None])) < 1e-14
 
 
+@pytest.mark.slow
 def test_mass_conserved_over_many_steps():
+    """Total mass over 50,000 forced steps with diffuse walls and a seeded
+    density field: constant to 1e-13 relative (collision and wall exact)."""
     ch = oracle.channel("D2V33", 4, 16, 24, 0.1, oracle.force_for_mach(0.1))
     ch.init(rho_field(16, 24, seed=7))
     m0 = ch.f.sum()
-    ch.step(2000)
+    ch.step(50000)
     assert abs(ch.f.sum() - m0) < 1e-13 * m0
 
 
@@ -307,6 +311,28 @@ def test_wall_exact_model_near_dsmc():
     conv, _, _ = ch.run_to_steady(1e-11, 50000)
     assert conv
     assert abs(ch.mass_flow() / 1.76 - 1) < 0.03
+
+
+def test_s1_models_mass_flow_follows_wall_moment_error():
+    """Sect. VI.A: within the S1 bulk models the mass flow at Kn = 0.4514
+    falls as sigma_zxx grows (the paper finds a correlation of -0.98 over
+    4677 models), and the model with the smallest |sigma_zxx|, D3V66
+    (Tab. bulk: -0.0001), lies near the DSMC value 1.76 (3 % band at
+    Ny = 64).  (x, z) marginals; sigma_zxx of D3V64, D3V66, D3V59 from
+    Tab. bulk."""
+    Kn = 0.4514
+    sig = {"D3V64xz": -0.0258, "D3V66xz": -0.0001, "D3V59xz": 0.0658}
+    mdot = {}
+    for name in sig:
+        ch = oracle.channel(name, 3, 1, 64, Kn, oracle.force_for_mach(Kn)).init()
+        conv, _, _ = ch.run_to_steady(1e-11, 50000)
+        assert conv
+        mdot[name] = ch.mass_flow()
+    assert abs(mdot["D3V66xz"] / 1.76 - 1) < 0.03
+    x = np.array([sig[n] for n in sig])
+    y = np.array([mdot[n] for n in sig])
+    assert np.corrcoef(x, y)[0, 1] < -0.8
+    assert min(mdot, key=lambda n: abs(mdot[n] - 1.76)) == "D3V66xz"
 
 
 def test_fixed_point_by_newton_on_tiny_grid():

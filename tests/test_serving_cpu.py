@@ -306,6 +306,7 @@ def test_precision_router_risk_and_lanes():
     from paper_1510_08886_gb300.serving import PrecisionRouter, relaxation_steps
     sets = {"D2V16": (None, None, 1.5)}
     router = PrecisionRouter(sets, chunk=100, du_noise=2e-10, risk=1e-3)
+    assert PrecisionRouter(sets).risk == 1e-4
     r_fast = Request(0, 0.0, "D2V16", 3, 1, 16, 1.0, 1e-6)
     r_slow = Request(1, 0.0, "D2V16", 3, 1, 2000, 0.01, 1e-6)
     r_tight = Request(2, 0.0, "D2V16", 3, 1, 64, 0.1, 1e-8)
