@@ -339,7 +339,8 @@ def test_marginal_models_steady_state_fp64(name, Kn):
 
 def test_marginal_s4_engine_kn_sweep_fp32():
     """The D3V112 (x, z) marginal (a compiled set) in the fp32 engine at
-    three Kn: steady mass flow within 1e-4 of the fp64 oracle."""
+    three Kn, run to max|du| < 1e-9 (fp32 storage resolves du only to about
+    1e-10): steady mass flow within 1e-4 of the fp64 oracle's steady state."""
     import paper_1510_08886_gb300 as lbm
     e, w, c = lbm.dvm("D3V112xz")
     eng = lbm.Engine("fp32", max_solves=4, arena_bytes=64 << 20)
@@ -349,7 +350,7 @@ def test_marginal_s4_engine_kn_sweep_fp32():
     mdot = {}
     for _ in range(1000):
         res = eng.run(1)
-        for sl in [sl for sl in live if res[sl, 0] < 1e-10]:
+        for sl in [sl for sl in live if res[sl, 0] < 1e-9]:
             mdot[live.pop(sl)] = float(res[sl, 1])
             eng.remove(sl)
         if not live:
