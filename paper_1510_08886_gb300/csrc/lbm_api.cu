@@ -183,6 +183,9 @@ void fill_params_impl(const lbm::SolveSpec* s, KParams<C>& k) {
     k.maxex = s->maxex;
     k.set_id = s->set_id;
     k.force = s->g != 0.0;
+    // k_step_ct's wall strips: four wall rows per wall (compiled sets with
+    // max|e_y| = 4), whole blocks per row, no row within reach of both walls
+    k.strips = (s->set_id >= 0 && s->maxey == 4 && s->Nx % 128 == 0 && s->Ny >= 8) ? s->Nx / 32 : 0;
     k.emit = 0;
     k.plane = (long long)s->Nx * s->Ny;
     const double omega = s->dt / (s->tau + 0.5 * s->dt);   // Eq. nm.8

@@ -39,6 +39,7 @@ struct KParams {
     int maxex;                   // max |e_x|
     int set_id;                  // compiled velocity set (dvm_sets.h), -1: generic
     int force;                   // 1 if g != 0
+    int strips;                  // wall blocks as 32-column x 4-row strips: Nx / 32, or 0
     int emit;                    // 1: write fp64 rho, u of this step; 2: add them
     unsigned int seed;           // step counter: stochastic rounding of 16-bit stores
     long long plane;             // elements per plane = ncell

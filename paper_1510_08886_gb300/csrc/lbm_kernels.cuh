@@ -482,6 +482,32 @@ __device__ __forceinline__ void pull_wall_ct(const KParams<C>& k, const S* __res
     ((f[I] = wall_value<SET, S, C, I>(k, src, x, y, pb, pt)), ...);
 }
 
+// e_y of plane a of a compiled set (rest, the P pair members, their negatives)
+template <class SET>
+__host__ __device__ constexpr int plane_ey_ct(int a) {
+    return a < SET::R ? 0 : (a < SET::R + SET::P ? SET::ey[a - SET::R] : -SET::ey[a - SET::R - SET::P]);
+}
+
+// Populations of a node in the four rows next to one wall, the wall's dPsi
+// given: the fill where the source lies beyond that wall, the pull otherwise
+// (the other wall is out of reach, Ny >= 8).
+template <class SET, typename S, typename C, bool BOTTOM, int A>
+__device__ __forceinline__ C strip_value(const KParams<C>& k, const S* __restrict__ src, int x, int y,
+                                         C dpsi) {
+    constexpr int EY = plane_ey_ct<SET>(A);
+    const int ys = y - EY;
+    if (BOTTOM ? ys < 0 : ys >= k.Ny) return fill_val<S, C>(k, dpsi, A);
+    int xs = x - k.sx[A];
+    xs += (xs < 0) ? k.Nx : 0;
+    return ld_val<S, C>(src[(long long)A * k.plane + (long long)ys * k.Nx + xs]);
+}
+
+template <class SET, typename S, typename C, bool BOTTOM, int... I>
+__device__ __forceinline__ void strip_values(const KParams<C>& k, const S* __restrict__ src, int x, int y,
+                                             C dpsi, C* f, std::integer_sequence<int, I...>) {
+    ((f[I] = strip_value<SET, S, C, BOTTOM, I>(k, src, x, y, dpsi)), ...);
+}
+
 // ---- compile-time velocity sets ---------------------------------------------
 // With e known at compile time, products with e components 0 and +-1 vanish
 // or become additions (IEEE rules forbid the compiler from folding x * 0).
@@ -868,6 +894,76 @@ __device__ __forceinline__ void pull_rows_any(const KParams<C>& k, const PTR& sp
         pull_rows<V, S, C>(k, sp, cell, f);
 }
 
+// ---- wall strips ------------------------------------------------------------
+// With four wall rows (max|e_y| = 4) every node of the rows 0..3 of a column
+// needs the same flux balance dPsi(x) of its wall, which wall_dpsi_ct sums
+// from ~26 fp64 terms on four interleaved accumulators (term t into
+// accumulator t mod 4).  A strip block covers 32 columns x the 4 wall rows of
+// one wall: warp r (one row) sums accumulator r's terms for its 32 columns,
+// in the same order, and the four partial sums meet in shared memory as
+// (a0 + a1) + (a2 + a3): the bits of wall_dpsi_ct at a quarter of the work.
+
+template <class SET, bool BOTTOM, int RR, class TERM, int A>
+__device__ __forceinline__ void strip_add_plane(double& acc, const TERM& term) {
+    constexpr int ey = plane_ey_ct<SET>(A);
+    if constexpr (BOTTOM ? ey < 0 : ey > 0) {
+        constexpr int n = BOTTOM ? -ey : ey;
+        constexpr int t0 = wall_terms_before<SET, BOTTOM>(A);
+#pragma unroll
+        for (int j = 0; j < n; ++j)
+            if (((t0 + j) & 3) == RR) acc += term(std::integral_constant<int, A>{}, j);
+    }
+}
+
+template <class SET, bool BOTTOM, int RR, class TERM, int... I>
+__device__ __forceinline__ double strip_partial(const TERM& term, std::integer_sequence<int, I...>) {
+    double acc = 0.0;
+    (strip_add_plane<SET, BOTTOM, RR, TERM, I>(acc, term), ...);
+    return acc;
+}
+
+template <class SET, int N, typename S, typename C, bool BOTTOM>
+__device__ __forceinline__ void wall_strip(const KParams<C>& k, const S* __restrict__ src, int strip,
+                                           const DevBufs& b) {
+    constexpr int R = SET::R, P = SET::P, V = R + 2 * P;
+    __shared__ double part[4][32];
+    const int r = threadIdx.x >> 5;                 // warp = wall row offset (nearest first)
+    const int lane = threadIdx.x & 31;
+    const int x = strip * 32 + lane;
+    const int y = BOTTOM ? r : k.Ny - 1 - r;
+    auto term = [&](auto bc, int j) {
+        constexpr int bb = decltype(bc)::value;
+        int xs = x - k.sx[bb];
+        xs += (xs < 0) ? k.Nx : 0;
+        const int row = BOTTOM ? j : (k.Ny - 1 - j);
+        return (double)ld_pop<S, C>(k, src[(long long)bb * k.plane + (long long)row * k.Nx + xs], bb);
+    };
+    constexpr auto seq = std::make_integer_sequence<int, V>{};
+    double acc;
+    switch (r) {                                    // warp-uniform
+        case 0: acc = strip_partial<SET, BOTTOM, 0>(term, seq); break;
+        case 1: acc = strip_partial<SET, BOTTOM, 1>(term, seq); break;
+        case 2: acc = strip_partial<SET, BOTTOM, 2>(term, seq); break;
+        default: acc = strip_partial<SET, BOTTOM, 3>(term, seq); break;
+    }
+    part[r][lane] = acc;
+    __syncthreads();
+    const C dpsi = C(((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) * k.inv_den);
+    const int cell = y * k.Nx + x;
+    C f[V];
+    strip_values<SET, S, C, BOTTOM>(k, src, x, y, dpsi, f, seq);
+    C drho, Jx = 0, Jy = 0, Kxx = 0, Kxy = 0, Kyy = 0;
+    moments_ct<SET, S, C>(k, f, drho, Jx, Jy, Kxx, Kxy, Kyy, std::make_integer_sequence<int, P>{});
+    const CellCoef<C> q = cell_coef<N, C>(k, drho, Jx, Jy, Kxx, Kxy, Kyy);
+    relax_ct<SET, N, S, C>(k, q, f);
+    S out[V];
+    pack_ct<SET, S, C>(f, sr_seed<S, C>(k.seed, cell), out);
+#pragma unroll
+    for (int a = 0; a < V; ++a) static_cast<S*>(k.dstp[a])[cell] = out[a];
+    emit_moments<C>(k, q, cell, b);
+    flag_density<C>(q, b.status);
+}
+
 // Fused step for a compiled velocity set: the V populations stay in registers
 // between the moment pass and the relaxation pass.
 //  - fast path (block-uniform): the block's nodes lie in one row at least
@@ -882,7 +978,22 @@ __global__ void __launch_bounds__(kBlock, min_blocks_for(SET::R + 2 * SET::P, si
 k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __restrict__ dst,
           const DevBufs b) {
     constexpr int R = SET::R, P = SET::P, V = R + 2 * P;
-    const int c0 = blockIdx.x * kBlock;
+    // With wall strips the grid starts with the bottom and the top strips (the
+    // heavier blocks run first, the uniform interior blocks form the tail);
+    // block 2 strips + m then takes the interior block at node (strips + m) 128.
+    int blk = int(blockIdx.x);
+    if (k.strips) {
+        if (blk < k.strips) {
+            wall_strip<SET, N, S, C, true>(k, src, blk, b);
+            return;
+        }
+        if (blk < 2 * k.strips) {
+            wall_strip<SET, N, S, C, false>(k, src, blk - k.strips, b);
+            return;
+        }
+        blk -= k.strips;
+    }
+    const int c0 = blk * kBlock;
     const int cell = c0 + threadIdx.x;
     const int y0 = c0 / k.Nx;
     const int x0 = c0 - y0 * k.Nx;
@@ -890,8 +1001,15 @@ k_step_ct(const __grid_constant__ KParams<C> k, const S* __restrict__ src, S* __
                       y0 < k.Ny - k.maxey;
     const int y1 = (min(c0 + kBlock, k.ncell) - 1) / k.Nx;
     const bool rows = !fast && y0 >= k.maxey && y1 < k.Ny - k.maxey;
+    bool wfast = fast;
+    if (rows) {   // a warp of one row away from both x ends pulls at fixed offsets
+        const int y = cell / k.Nx, x = cell - y * k.Nx;
+        const int ylead = __shfl_sync(0xffffffffu, y, 0);
+        wfast = __all_sync(0xffffffffu, cell < k.ncell && x >= k.maxex && x < k.Nx - k.maxex &&
+                                            y == ylead);
+    }
     C f[V];
-    if (fast) {
+    if (wfast) {
 #pragma unroll
         for (int a = 0; a < V; ++a) f[a] = ld_val<S, C>(ld_stream(static_cast<const S*>(k.srcf[a]) + cell));
     } else if (rows) {
