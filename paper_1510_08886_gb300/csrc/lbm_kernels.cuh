@@ -120,17 +120,9 @@ __device__ __forceinline__ double ld_stream(const double* p) {
     asm("ld.global.nc.L2::256B.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 }
-// 16-bit planes: a warp's load is only 64 bytes, so the 256-byte L2 fill
-// brings the next three warps' data as well
-__device__ __forceinline__ __half ld_stream(const __half* p) {
-    unsigned short v;
-    asm("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
-    return __ushort_as_half(v);
-}
-__device__ __forceinline__ __nv_bfloat16 ld_stream(const __nv_bfloat16* p) {
-    unsigned short v;
-    asm("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
-    return __ushort_as_bfloat16(v);
+template <typename S>
+__device__ __forceinline__ S ld_stream(const S* p) {      // 16-bit planes: plain load
+    return *p;
 }
 
 template <typename S, typename C>
