@@ -154,3 +154,14 @@ def test_compiled_set_header_is_current():
         e, w, c = lbm.dvm(tname + ("xz" if marg else ""))
         rest, pos = gen.pairs_of({tuple(v) for v in e.tolist()})
         assert len(pos) * 2 + rest == len(e)
+
+
+def test_average_and_fma_rate_validate_before_any_device_call(L):
+    """lbm_average and lbm_fma_rate reject bad arguments with LBM_EINVAL
+    before touching a device (so this runs without a GPU)."""
+    lib = L.lib()
+    out = ctypes.c_double(0.0)
+    assert lib.lbm_average(None, 10, 1) == L.LBM_EINVAL
+    assert lib.lbm_fma_rate(L.LBM_FP16, None, ctypes.byref(out)) == L.LBM_EINVAL
+    assert lib.lbm_fma_rate(7, None, ctypes.byref(out)) == L.LBM_EINVAL
+    assert lib.lbm_fma_rate(L.LBM_FP64, None, None) == L.LBM_EINVAL

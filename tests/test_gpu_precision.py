@@ -148,3 +148,27 @@ def test_fp16_checkpoint_resume_bitwise():
     a.step(77)
     b = lbm.Solver(e, w, c, 3, 1, 64, Kn, g, precision="fp16").set_state(blob).step(77)
     assert np.array_equal(a.populations(), b.populations())
+
+
+def test_average_rejects_bad_windows():
+    import paper_1510_08886_gb300 as lbm
+    from paper_1510_08886_gb300 import _lib
+    e, w, c = lbm.dvm("D2V16")
+    s = lbm.Solver(e, w, c, 3, 1, 16, 0.1, oracle.force_for_mach(0.1), precision="fp16").init()
+    L = _lib.lib()
+    assert L.lbm_average(s.handle, 5, 10) == _lib.LBM_EINVAL      # fewer steps than one sample
+    assert L.lbm_average(s.handle, 10, 0) == _lib.LBM_EINVAL
+    assert L.lbm_average(s.handle, 10, 5) == _lib.LBM_OK
+    assert s.steps == 10
+
+
+def test_fma_rate_probe():
+    """The measured fp64 FMA rate lies between a tenth and twice the nominal
+    GB300 figure (152 SMs x 2 DFMA per clock x 2 flops at up to 2.07 GHz),
+    and fp32 runs far faster than fp64 on this part."""
+    import paper_1510_08886_gb300 as lbm
+    r64 = lbm.fma_rate("fp64")
+    r32 = lbm.fma_rate("fp32")
+    nominal = 152 * 2 * 2 * 2.07e9
+    assert 0.1 * nominal < r64 < 2.0 * nominal
+    assert r32 > 10 * r64
