@@ -84,9 +84,11 @@ def test_fp64_parity_after_steps(name, N, Nx, Ny):
 @pytest.mark.parametrize("name,N", [("D2V33", 4), ("D2V16", 3), ("D2V32", 3), ("D3V107xz", 3)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_parity_interior_fast_path(name, N, precision):
-    """Nx = 1024: full 256-node blocks in interior rows take the fixed-offset
-    pull path, the blocks at x = 0 and x = Nx - 256 the wrapping path, wall
-    rows the wall path; all three must agree with the oracle."""
+    """Nx = 1024: 128-node blocks in interior rows take the fixed-offset pull
+    path, the blocks at x = 0 and x = Nx - 128 the wrapping path (their warps
+    away from the ends at fixed offsets), the wall rows the wall path -- for
+    the sets with four wall rows as 32-column strips; all must agree with the
+    oracle."""
     Nx, Ny, Kn = 1024, 30, 0.2
     g = oracle.force_for_mach(Kn, 1e-2)
     rho = rho_field(Nx, Ny, seed=21)
