@@ -349,11 +349,31 @@ int lbm_engine_run(lbm_engine* e, int chunks, double* results);
 int lbm_engine_launch(lbm_engine* e, int chunks);
 int lbm_engine_wait(lbm_engine* e, double* results);
 
-/* Time candidate launch shapes (fraction of the occupancy limit used for the
- * persistent grid x tiles taken per grab) on the resident solves and keep
- * the fastest.  The timed chunks advance the solves (3 chunks per candidate,
- * counted in their step counters). */
+/* Time candidate schedules of the tiled kernel on the resident solves and
+ * keep the fastest: first the tile shape and cells per tile (linear tiles of
+ * 128, 256 or 512 consecutive nodes; rectangles 32, 64 or 128 columns wide of
+ * 128, 256 or 512 nodes) at the current grid, then the persistent grid (1 or
+ * 1/2 of the occupancy limit) x tiles taken per grab (1..16) at the best
+ * shape.  The schedule decides which block updates a node, never the node's
+ * arithmetic: results are bitwise the same under every schedule.  The timed
+ * chunks advance the solves (3 chunks per candidate, 21 candidates, counted in
+ * their step counters).  *best_ms_per_step (may be NULL) receives the time of
+ * one step of the best candidate. */
 int lbm_engine_autotune(lbm_engine* e, double* best_ms_per_step);
+
+/* Set or read the schedule the autotuner chooses.  tile_width: 0 for linear
+ * tiles (consecutive nodes in row-major order), else 32, 64 or 128 columns (a
+ * solve whose Nx is not a multiple of it, or whose Ny is below the tile's
+ * rows, takes linear tiles); tile_cells: nodes per tile, 128, 256 or 512;
+ * grab: tiles taken per atomic grab, 1..64; grid_fraction: fraction of the
+ * occupancy limit used for the persistent grid, (0, 1].  LBM_EINVAL for other
+ * values or while launches are outstanding.  Takes effect at the next
+ * lbm_engine_run or lbm_engine_launch.  Any pointer of the getter may be
+ * NULL. */
+int lbm_engine_set_schedule(lbm_engine* e, int tile_width, int tile_cells, int grab,
+                            double grid_fraction);
+int lbm_engine_get_schedule(const lbm_engine* e, int* tile_width, int* tile_cells, int* grab,
+                            double* grid_fraction);
 
 /* Steps done by a slot and its status (LBM_OK or LBM_ENONFINITE). */
 int lbm_engine_info(lbm_engine* e, int slot, long* steps, int* status);

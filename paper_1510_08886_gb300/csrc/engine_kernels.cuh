@@ -1,10 +1,11 @@
 // Device code of the multi-solve engine: one time step of many independent
 // channels in one persistent launch per compiled velocity set.
 //
-// Work is a list of tiles (solve slot, first node) of kBlock consecutive
-// nodes of one channel.  Blocks of a fixed, SM-filling grid take `chunk`
-// tiles at a time from an atomic counter, so small and large channels, wall
-// tiles and interior tiles balance across the GPU.  Each tile runs the same
+// Work is a list of tiles (solve slot, first node, shape) of one channel:
+// m kBlock consecutive nodes, or a rectangle of tw columns x m kBlock / tw
+// rows.  Blocks of a fixed, SM-filling grid take `chunk` tiles at a time from
+// an atomic counter, so small and large channels, wall tiles and interior
+// tiles balance across the GPU.  Each tile runs the same
 // arithmetic as the single-solve kernel k_step_ct (pull + walls + moments +
 // relaxation), with the solve's constants read from its device record.
 #pragma once
@@ -28,9 +29,18 @@ struct EngineSolve {
     double kn, tau, g;      // for mdot = 2 tau <u_x> / (g Kn)
 };
 
+// A tile: m = 2^lm sub-tiles of kBlock nodes of one channel (m = 1, 2 or 4,
+// the same for every tile of a launch).  Linear tiles (tws = 0) are m kBlock
+// consecutive nodes from cell0 in row-major order, sub-tile j the j-th run of
+// kBlock; 2-D tiles (tws = 5, 6 or 7: width tw = 2^tws columns, Nx a multiple
+// of tw) are tw columns x m kBlock / tw rows from node cell0 = y0 Nx + x0,
+// sub-tile j the j-th band of kBlock / tw rows.  Thread i of the block
+// updates node i of each sub-tile (column x0 + i mod tw of a 2-D tile).  The
+// shape only changes which block updates a node, never the node's arithmetic.
 struct EngineTile {
     int slot;
     int cell0;
+    int tws;
 };
 
 // Registers per thread allowed beyond the populations' share (min_blocks_for),
@@ -61,7 +71,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks_for(SET::R + 2 * SET::P + e
 k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __restrict__ tiles,
               const int* __restrict__ ntiles_p, const int* __restrict__ tile_off_p,
               int* __restrict__ counter,
-              const unsigned int* __restrict__ seed_p, int parity, int emit, int chunk) {
+              const unsigned int* __restrict__ seed_p, int parity, int emit, int chunk, int lm) {
     constexpr int R = SET::R, P = SET::P, V = R + 2 * P;
     __shared__ const S* sp[V];
     __shared__ S* dp[V];
@@ -78,8 +88,10 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
         const int first = s_first;
         if (first >= ntiles) break;
         const int last = min(first + chunk, ntiles);
-        for (int t = first; t < last; ++t) {
-            const EngineTile tile = tiles[t];
+        // sub-tiles u of the tiles [first, last)
+        for (int u = first << lm; u < (last << lm); ++u) {
+            const EngineTile tile = tiles[u >> lm];
+            const int j = u & ((1 << lm) - 1);
             const EngineSolve<C>& B = solves[tile.slot];
             const KParams<C>& k = s_k;
             if (tile.slot != cur_slot) {
@@ -101,21 +113,38 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
                 cur_slot = tile.slot;
             }
             const S* src = sp[0] + k.off[0];   // lattice base of the current state
-            const int c0 = tile.cell0;
-            const int cell = c0 + threadIdx.x;
-            const int y0 = c0 / k.Nx;
-            const int x0 = c0 - y0 * k.Nx;
-            const bool fast = x0 >= k.maxex && x0 + kBlock - 1 + k.maxex < k.Nx &&
-                              y0 >= k.maxey && y0 < k.Ny - k.maxey;
-            const int y1 = (min(c0 + kBlock, k.ncell) - 1) / k.Nx;
-            const bool rows = !fast && y0 >= k.maxey && y1 < k.Ny - k.maxey;
+            // node of this thread in sub-tile j; fast = every node of the
+            // sub-tile pulls at fixed offsets; rows = no node is near a wall
+            int cell, ya, yb;
+            bool fast;
+            if (tile.tws == 0) {
+                const int cs = tile.cell0 + j * kBlock;
+                cell = cs + int(threadIdx.x);
+                ya = cs / k.Nx;
+                const int xa = cs - ya * k.Nx;
+                yb = (min(cs + kBlock, k.ncell) - 1) / k.Nx;
+                fast = xa >= k.maxex && xa + kBlock - 1 + k.maxex < k.Nx && ya >= k.maxey &&
+                       ya < k.Ny - k.maxey;
+            } else {
+                const int tws = tile.tws;
+                const int y0 = tile.cell0 / k.Nx;
+                const int x0 = tile.cell0 - y0 * k.Nx;
+                ya = y0 + j * (kBlock >> tws);              // kBlock / tw rows per sub-tile
+                yb = min(ya + (kBlock >> tws), k.Ny) - 1;
+                cell = (ya + (int(threadIdx.x) >> tws)) * k.Nx + x0 + (int(threadIdx.x) & ((1 << tws) - 1));
+                fast = x0 >= k.maxex && x0 + (1 << tws) - 1 + k.maxex < k.Nx && ya >= k.maxey &&
+                       ya + (kBlock >> tws) - 1 < k.Ny - k.maxey;
+            }
+            // a node beyond the channel (cell >= ncell: past the last node, or
+            // a row at or above Ny of a 2-D tile) has nothing to do
             if (!fast && cell >= k.ncell) continue;
+            const bool rows = !fast && ya >= k.maxey && yb < k.Ny - k.maxey;
             C f[V];
             if (fast) {
 #pragma unroll
                 for (int a = 0; a < V; ++a) f[a] = ld_val<S, C>(ld_stream(sp[a] + cell));
             } else if (rows || (cell / k.Nx >= k.maxey && cell / k.Nx < k.Ny - k.maxey)) {
-                // nodes away from the walls (the whole tile, or this node of a wall tile)
+                // nodes away from the walls (the whole sub-tile, or this node of a wall tile)
                 pull_rows_any<SET, S, C>(k, sp, cell, f);
             } else {
                 const int y = cell / k.Nx;

@@ -21,6 +21,7 @@ struct EngineLaunch {
     int* counter;              // work counter of this (step, group)
     const unsigned* seed;
     int parity, emit, chunk;
+    int lm;                    // log2 of the sub-tiles per tile
     int grid;
 };
 
@@ -29,7 +30,7 @@ cudaError_t engine_step_one(const EngineLaunch& L, cudaStream_t st) {
     using C = CompOf<S>;
     k_engine_step<SET, N, S, C><<<L.grid, kBlock, 0, st>>>(
         static_cast<const EngineSolve<C>*>(L.solves), L.tiles, L.ntiles, L.tile_off, L.counter, L.seed,
-        L.parity, L.emit, L.chunk);
+        L.parity, L.emit, L.chunk, L.lm);
     return cudaGetLastError();
 }
 

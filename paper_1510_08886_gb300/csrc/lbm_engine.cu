@@ -176,6 +176,8 @@ struct lbm_engine {
     int K = 100;
     double bps_factor = 1.0;   // fraction of the occupancy limit used for the grid
     int grab = 4;              // tiles taken per atomic grab
+    int tile_tws = 0;          // tile width 2^tws columns (0: linear tiles)
+    int tile_m = 1;            // tile of tile_m x 128 nodes
     int sms = 0;
     bool tiles_dirty = true, graph_dirty = true;
     // resident chunks
@@ -322,8 +324,17 @@ int rebuild_tiles(lbm_engine* e) {
                 res.push_back(s);
                 continue;
             }
-            const int n = sl.spec.Nx * sl.spec.Ny;
-            for (int c0 = 0; c0 < n; c0 += lbm::kBlock) t.push_back({s, c0});
+            const int Nx = sl.spec.Nx, Ny = sl.spec.Ny, cells = e->tile_m * lbm::kBlock;
+            const int tw = e->tile_tws ? 1 << e->tile_tws : 0, th = tw ? cells / tw : 0;
+            if (tw && Nx % tw == 0 && Ny >= th) {
+                // at most 2 Nx Ny / cells tiles (Ny >= th)
+                for (int y0 = 0; y0 < Ny; y0 += th)
+                    for (int x0 = 0; x0 < Nx; x0 += tw)
+                        t.push_back({s, y0 * Nx + x0, e->tile_tws});
+            } else {
+                for (int c0 = 0; c0 < Nx * Ny; c0 += cells)
+                    t.push_back({s, c0, 0});
+            }
         }
         std::vector<ResItem> items;
         for (int s : res)
@@ -448,6 +459,7 @@ int enqueue_chunk(lbm_engine* e) {
             L.parity = i & 1;
             L.emit = i == e->K - 1 ? 1 : (i == e->K - 2 ? 2 : 0);
             L.chunk = e->grab;
+            L.lm = e->tile_m == 4 ? 2 : e->tile_m - 1;
             L.grid = w.grid;
             const int set = w.g / 3, N = w.g % 3 + 2;
             err = e->precision == LBM_FP16   ? lbm::engine_step_half(set, N, L, ts)
@@ -593,10 +605,10 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
     e->precision = precision;
     e->max_slots = max_solves;
     const size_t elem = lbm::elem_bytes(precision);
-    // tiles: at most one per 128 nodes of the smallest lattice that fits, plus a
-    // partial tile per solve
+    // tiles: at most two per 128 nodes of the smallest lattice that fits (2-D
+    // tiles clipped at the top row), plus a partial tile per solve
     const size_t max_cells = arena_bytes / (2 * 16 * elem);
-    e->tile_cap = max_cells / lbm::kBlock + size_t(max_solves) + 1;
+    e->tile_cap = 2 * (max_cells / lbm::kBlock) + size_t(max_solves) + 1;
     size_t off = 0;
     auto take = [&](size_t n) { size_t o = off; off = al256(off + n); return o; };
     e->rec_bytes = precision == LBM_FP64 ? sizeof(lbm::EngineSolve<double>)
@@ -836,45 +848,101 @@ int lbm_engine_run(lbm_engine* e, int chunks, double* results) {
     return fetch_results(e, results);
 }
 
+namespace {
+
+// Time two chunks of the current schedule (after a warm-up chunk); the three
+// chunks advance the solves and are counted.
+int time_schedule(lbm_engine* e, cudaEvent_t a, cudaEvent_t b, float* ms) {
+    int rc = prepare(e);
+    if (rc) return rc;
+    cudaGraphLaunch(e->exec, e->stream);      // warm-up chunk
+    cudaEventRecord(a, e->stream);
+    cudaGraphLaunch(e->exec, e->stream);
+    cudaGraphLaunch(e->exec, e->stream);
+    cudaEventRecord(b, e->stream);
+    if (cudaEventSynchronize(b) != cudaSuccess) return LBM_ECUDA;
+    cudaEventElapsedTime(ms, a, b);
+    for (auto& sl : e->slots)
+        if (sl.used) sl.steps += 3L * e->K;
+    return LBM_OK;
+}
+
+}  // namespace
+
+// Coordinate search: the tile shape and cells per tile at the current grid and
+// grab, then the grid fraction and grab at the best shape.
 int lbm_engine_autotune(lbm_engine* e, double* best_ms_per_step) {
     if (!e || e->pending) return LBM_EINVAL;
     int rc = prepare(e);
     if (rc) return rc;
     if (e->plan.empty()) return LBM_OK;
+    static const int shapes[][2] = {{0, 1}, {0, 2}, {0, 4}, {5, 1}, {5, 2}, {5, 4},
+                                    {6, 1}, {6, 2}, {6, 4}, {7, 2}, {7, 4}};
     const double factors[] = {1.0, 0.5};
     const int grabs[] = {1, 2, 4, 8, 16};
     double best = HUGE_VAL, bf = e->bps_factor;
-    int bg = e->grab;
+    int bg = e->grab, btws = e->tile_tws, bm = e->tile_m;
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess) return LBM_ECUDA;
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return LBM_ECUDA; }
+    for (const auto& sh : shapes) {
+        e->tile_tws = sh[0];
+        e->tile_m = sh[1];
+        e->tiles_dirty = true;
+        e->graph_dirty = true;
+        float ms = 0.f;
+        if ((rc = time_schedule(e, a, b, &ms))) break;
+        if (ms < best) { best = ms; btws = sh[0]; bm = sh[1]; }
+    }
+    e->tile_tws = btws;
+    e->tile_m = bm;
+    e->tiles_dirty = true;
+    e->graph_dirty = true;
     for (double f : factors) {
+        if (rc) break;
         for (int g : grabs) {
             e->bps_factor = f;
             e->grab = g;
-            if ((rc = recapture(e))) break;
-            cudaGraphLaunch(e->exec, e->stream);      // warm-up chunk
-            cudaEventRecord(a, e->stream);
-            cudaGraphLaunch(e->exec, e->stream);
-            cudaGraphLaunch(e->exec, e->stream);
-            cudaEventRecord(b, e->stream);
-            if (cudaEventSynchronize(b) != cudaSuccess) { rc = LBM_ECUDA; break; }
+            e->graph_dirty = true;
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, a, b);
-            for (auto& sl : e->slots)
-                if (sl.used) sl.steps += 3L * e->K;
+            if ((rc = time_schedule(e, a, b, &ms))) break;
             if (ms < best) { best = ms; bf = f; bg = g; }
         }
-        if (rc) break;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (rc) return rc;
     e->bps_factor = bf;
     e->grab = bg;
-    rc = recapture(e);
+    e->graph_dirty = true;
+    rc = prepare(e);
     if (best_ms_per_step) *best_ms_per_step = best / (2.0 * e->K);
     return rc;
+}
+
+int lbm_engine_set_schedule(lbm_engine* e, int tile_width, int tile_cells, int grab,
+                            double grid_fraction) {
+    if (!e || e->pending) return LBM_EINVAL;
+    if (tile_width != 0 && tile_width != 32 && tile_width != 64 && tile_width != 128) return LBM_EINVAL;
+    if (tile_cells != 128 && tile_cells != 256 && tile_cells != 512) return LBM_EINVAL;
+    if (grab < 1 || grab > 64 || !(grid_fraction > 0.0 && grid_fraction <= 1.0)) return LBM_EINVAL;
+    e->tile_tws = tile_width == 0 ? 0 : (tile_width == 32 ? 5 : (tile_width == 64 ? 6 : 7));
+    e->tile_m = tile_cells / lbm::kBlock;
+    e->grab = grab;
+    e->bps_factor = grid_fraction;
+    e->tiles_dirty = true;
+    e->graph_dirty = true;
+    return LBM_OK;
+}
+
+int lbm_engine_get_schedule(const lbm_engine* e, int* tile_width, int* tile_cells, int* grab,
+                            double* grid_fraction) {
+    if (!e) return LBM_EINVAL;
+    if (tile_width) *tile_width = e->tile_tws ? 1 << e->tile_tws : 0;
+    if (tile_cells) *tile_cells = e->tile_m * lbm::kBlock;
+    if (grab) *grab = e->grab;
+    if (grid_fraction) *grid_fraction = e->bps_factor;
+    return LBM_OK;
 }
 
 int lbm_engine_info(lbm_engine* e, int slot, long* steps, int* status) {

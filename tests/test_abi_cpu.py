@@ -165,3 +165,14 @@ def test_average_and_fma_rate_validate_before_any_device_call(L):
     assert lib.lbm_fma_rate(L.LBM_FP16, None, ctypes.byref(out)) == L.LBM_EINVAL
     assert lib.lbm_fma_rate(7, None, ctypes.byref(out)) == L.LBM_EINVAL
     assert lib.lbm_fma_rate(L.LBM_FP64, None, None) == L.LBM_EINVAL
+
+
+def test_engine_schedule_rejects_a_null_engine(L):
+    """The schedule setter and getter check the handle before anything else
+    (no device call)."""
+    lib = L.lib()
+    tw, tc, g = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    f = ctypes.c_double(0.0)
+    assert lib.lbm_engine_set_schedule(None, 32, 256, 4, 1.0) == L.LBM_EINVAL
+    assert lib.lbm_engine_get_schedule(None, ctypes.byref(tw), ctypes.byref(tc), ctypes.byref(g),
+                                       ctypes.byref(f)) == L.LBM_EINVAL

@@ -134,7 +134,11 @@ def test_autotune_keeps_results_exact():
     ms = a.autotune()
     assert ms > 0
     steps = a.info(sa[0])[0]
-    assert steps == 30 * 10       # 2 factors x 5 grabs x 3 chunks of 10
+    # 11 tile shapes + 2 grid fractions x 5 grabs, 3 chunks of 10 each
+    assert steps == 63 * 10
+    sched = a.schedule()
+    assert sched["tile_width"] in (0, 32, 64, 128) and sched["tile_cells"] in (128, 256, 512)
+    assert 1 <= sched["grab"] <= 16 and sched["grid_fraction"] in (0.5, 1.0)
     a.run(1)
     b.run(steps // 10 + 1)
     for x, y, spec in zip(sa, sb, MIX[:4]):
@@ -367,4 +371,52 @@ def test_fp64_engine_stops_with_the_oracle():
     assert conv and eng.info(slot)[0] == steps
     assert abs(res[slot, 1] / ref.mass_flow() - 1) < 1e-12
     assert abs(res[slot, 2] / ref.slip_velocity() - 1) < 1e-11
+    eng.close()
+
+
+SCHEDULE_MIX = [("D2V33", 4, 256, 40, 0.05), ("D3V107xz", 3, 64, 33, 0.3), ("D2V33", 4, 128, 9, 0.2),
+                ("D2V16", 3, 1, 64, 0.1), ("D3V107xz", 3, 256, 20, 0.01), ("D2V32", 3, 5, 30, 0.2),
+                ("D2V33", 4, 64, 129, 0.5), ("D3V96xz", 3, 96, 14, 0.7), ("D2V33", 4, 32, 300, 1.0)]
+SCHEDULES = [(0, 128, 4, 1.0), (0, 512, 1, 0.5), (32, 128, 2, 1.0), (32, 512, 8, 1.0),
+             (64, 256, 1, 1.0), (64, 512, 4, 0.5), (128, 256, 16, 1.0), (128, 512, 3, 1.0)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "fp64"])
+def test_schedules_bitwise_equal(precision):
+    """Tile shape, cells per tile, grab and grid only decide which block
+    updates a node: every schedule gives bitwise the same states, observables
+    and status.  The mix has channels that take 2-D tiles (Nx a multiple of
+    the width, Ny clipped by the tile's rows or not), channels that fall back
+    to linear tiles (Nx = 1, 5; Ny below the tile's rows), tall and short."""
+    import paper_1510_08886_gb300 as lbm
+    engines, slots = [], []
+    for tw, tc, grab, frac in SCHEDULES:
+        eng = lbm.Engine(precision, max_solves=16, arena_bytes=128 << 20, chunk=20, resident=False)
+        eng.set_schedule(tw, tc, grab, frac)
+        assert eng.schedule() == {"tile_width": tw, "tile_cells": tc, "grab": grab,
+                                  "grid_fraction": frac}
+        slots.append([_add(eng, s, seed=31 + i) for i, s in enumerate(SCHEDULE_MIX)])
+        engines.append(eng)
+    res = [eng.run(2).copy() for eng in engines]
+    for j in range(1, len(engines)):
+        for i, (name, N, Nx, Ny, Kn) in enumerate(SCHEDULE_MIX):
+            ma = engines[0].moments(slots[0][i], Nx, Ny)
+            mb = engines[j].moments(slots[j][i], Nx, Ny)
+            for a, b in zip(ma, mb):
+                assert np.array_equal(a, b), (SCHEDULES[j], SCHEDULE_MIX[i])
+            assert np.array_equal(res[0][slots[0][i]], res[j][slots[j][i]])
+            assert engines[0].info(slots[0][i], status=True) == engines[j].info(slots[j][i],
+                                                                                status=True)
+            assert np.array_equal(engines[0].get_state(slots[0][i]), engines[j].get_state(slots[j][i]))
+    for eng in engines:
+        eng.close()
+
+
+def test_schedule_validates():
+    import paper_1510_08886_gb300 as lbm
+    eng = lbm.Engine("fp32", max_solves=2, arena_bytes=16 << 20)
+    for bad in [(16, 128, 4, 1.0), (32, 64, 4, 1.0), (32, 1024, 4, 1.0), (0, 128, 0, 1.0),
+                (0, 128, 65, 1.0), (0, 128, 4, 0.0), (0, 128, 4, 1.5)]:
+        with pytest.raises(lbm.LBMError):
+            eng.set_schedule(*bad)
     eng.close()
