@@ -64,6 +64,37 @@ __device__ __forceinline__ CellCoef<C> res_collide(const KParams<C>& k, C* f) {
     return q;
 }
 
+// Copy the parts of a solve's constants that kernels of a compiled set read:
+// the scalars and the first V (per plane) or P (per pair) entries of every
+// array; the arrays are sized for LBM_MAX_V, so this moves about a third of
+// the record.
+template <class SET, typename C>
+__device__ __forceinline__ void copy_params(const KParams<C>& src, KParams<C>& dst) {
+    using K = KParams<C>;
+    constexpr int V = SET::R + 2 * SET::P, P = SET::P;
+    constexpr int cv = int(sizeof(C) / 4) * V, cp = int(sizeof(C) / 4) * P;
+    // (first 4-byte word, words)
+    constexpr int seg[][2] = {
+        {0, int(offsetof(K, ex) / 4)},
+        {int(offsetof(K, ex) / 4), V}, {int(offsetof(K, ey) / 4), V}, {int(offsetof(K, sx) / 4), V},
+        {int(offsetof(K, off) / 4), V}, {int(offsetof(K, dx) / 4), V},
+        {int(offsetof(K, srcf) / 4), 2 * V}, {int(offsetof(K, dstp) / 4), 2 * V},
+        {int(offsetof(K, w) / 4), 2 * V},
+        {int(offsetof(K, cw) / 4), cv}, {int(offsetof(K, sw) / 4), cv}, {int(offsetof(K, isw) / 4), cv},
+        {int(offsetof(K, hw) / 4), cp}, {int(offsetof(K, hwx) / 4), cp}, {int(offsetof(K, hwy) / 4), cp},
+        {int(offsetof(K, hwxx) / 4), cp}, {int(offsetof(K, hwxy) / 4), cp}, {int(offsetof(K, hwyy) / 4), cp},
+        {int(offsetof(K, hw_rest) / 4), int((offsetof(K, pex) - offsetof(K, hw_rest)) / 4)},
+        {int(offsetof(K, pex) / 4), cp}, {int(offsetof(K, pey) / 4), cp}, {int(offsetof(K, pexx) / 4), cp},
+        {int(offsetof(K, pexy2) / 4), cp}, {int(offsetof(K, peyy) / 4), cp}, {int(offsetof(K, pge) / 4), cp},
+        {int(offsetof(K, pomw) / 4), cp},
+        {int(offsetof(K, omw_rest) / 4), int((sizeof(K) - offsetof(K, omw_rest)) / 4)}};
+    const int* s = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(&dst);
+#pragma unroll
+    for (int g = 0; g < int(sizeof(seg) / sizeof(seg[0])); ++g)
+        for (int i = int(threadIdx.x); i < seg[g][1]; i += kBlock) d[seg[g][0] + i] = s[seg[g][0] + i];
+}
+
 // emit: 0 = nothing, 1 = rho, u_x, u_y into the moment fields, 2 = u_x into prev
 template <class SET, int N, typename S, typename C>
 __global__ void __launch_bounds__(kBlock, min_blocks_for(SET::R + 2 * SET::P + engine_extra_regs<SET>(),
@@ -75,17 +106,19 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
     constexpr int R = SET::R, P = SET::P, V = R + 2 * P;
     __shared__ const S* sp[V];
     __shared__ S* dp[V];
-    __shared__ int s_first;
+    __shared__ int s_first[2];
     __shared__ KParams<C> s_k;
     const int ntiles = *ntiles_p;
     tiles += *tile_off_p;
     const unsigned seed = *seed_p + unsigned(parity);
     int cur_slot = -1;
-    for (;;) {
+    // One barrier per grab: every thread reads grab i's first tile from
+    // s_first[i & 1] before it reaches the barrier of grab i + 1, after which
+    // thread 0 may overwrite that entry (at grab i + 2).
+    for (int it = 0;; ++it) {
+        if (threadIdx.x == 0) s_first[it & 1] = atomicAdd(counter, chunk);
         __syncthreads();
-        if (threadIdx.x == 0) s_first = atomicAdd(counter, chunk);
-        __syncthreads();
-        const int first = s_first;
+        const int first = s_first[it & 1];
         if (first >= ntiles) break;
         const int last = min(first + chunk, ntiles);
         // sub-tiles u of the tiles [first, last)
@@ -95,19 +128,18 @@ k_engine_step(const EngineSolve<C>* __restrict__ solves, const EngineTile* __res
             const EngineSolve<C>& B = solves[tile.slot];
             const KParams<C>& k = s_k;
             if (tile.slot != cur_slot) {
+                // The previous slot's constants and plane bases are free once
+                // every thread is past its last sub-tile: at the grab's
+                // barrier for the grab's first sub-tile, else at this one.
+                if (u != (first << lm)) __syncthreads();
+                copy_params<SET, C>(B.k, s_k);
                 // per-plane pull bases (interior offset folded in) and store bases
-                __syncthreads();
-                {
-                    const int* srcw = reinterpret_cast<const int*>(&B.k);
-                    int* dstw = reinterpret_cast<int*>(&s_k);
-                    for (int i = threadIdx.x; i < int(sizeof(KParams<C>) / 4); i += kBlock) dstw[i] = srcw[i];
-                }
-                __syncthreads();
                 const int cur = B.phase ^ parity;
                 if (threadIdx.x < V) {
                     const int a = threadIdx.x;
-                    sp[a] = static_cast<const S*>(B.f[cur]) + (long long)a * k.plane - k.off[a];
-                    dp[a] = static_cast<S*>(B.f[cur ^ 1]) + (long long)a * k.plane;
+                    const long long plane = B.k.plane;
+                    sp[a] = static_cast<const S*>(B.f[cur]) + (long long)a * plane - B.k.off[a];
+                    dp[a] = static_cast<S*>(B.f[cur ^ 1]) + (long long)a * plane;
                 }
                 __syncthreads();
                 cur_slot = tile.slot;
