@@ -216,11 +216,15 @@ def batched_section(lbm, torch):
     step_bytes = sum(2 * len(sets[it["dvm"]][1]) * 4 * it["Nx"] * it["Ny"] for it in work)
     need = sum(lbm.Engine.solve_bytes(*sets[it["dvm"]], it["Nx"], it["Ny"], "fp32") for it in work)
     eng = lbm.Engine("fp32", max_solves=256, arena_bytes=need + (64 << 20), chunk=100)
+    tiled_slot = {}
     for it in work:
         e, w, c = sets[it["dvm"]]
-        assert eng.add(e, w, c, it["order"], it["Nx"], it["Ny"], it["Kn"],
-                       lbm.force_for_mach(it["Kn"])) is not None
+        slot = eng.add(e, w, c, it["order"], it["Nx"], it["Ny"], it["Kn"], lbm.force_for_mach(it["Kn"]))
+        assert slot is not None
+        if it["Nx"] > 1:
+            tiled_slot.setdefault(it["dvm"], slot)
     eng.autotune()
+    schedule = {d: eng.schedule(sl) for d, sl in tiled_slot.items()}
     eng.run(2)
     torch.cuda.synchronize()
     chunks = 10
@@ -250,6 +254,7 @@ def batched_section(lbm, torch):
     return {"workload": "256 channels, seed 20151030: Ny U{16..512}, Nx {1,64,256}, Kn log-U[0.01,1], "
                         "D2V33 N=4 / D3V107xz N=3, fp32",
             "cells": cells, "GLUPS_engine": batched, "GLUPS_per_solve_api": per_solve,
+            "autotuned_schedule": schedule,
             "speedup": batched / per_solve, "timed_steps": chunks * 100,
             "bytes_per_step": step_bytes,
             "achieved_GBs": step_bytes * batched * 1e9 / cells / 1e9,

@@ -350,30 +350,37 @@ int lbm_engine_launch(lbm_engine* e, int chunks);
 int lbm_engine_wait(lbm_engine* e, double* results);
 
 /* Time candidate schedules of the tiled kernel on the resident solves and
- * keep the fastest: first the tile shape and cells per tile (linear tiles of
- * 128, 256 or 512 consecutive nodes; rectangles 32, 64 or 128 columns wide of
- * 128, 256 or 512 nodes) at the current grid, then the persistent grid (1 or
- * 1/2 of the occupancy limit) x tiles taken per grab (1..16) at the best
- * shape.  The schedule decides which block updates a node, never the node's
- * arithmetic: results are bitwise the same under every schedule.  The timed
- * chunks advance the solves (3 chunks per candidate, 21 candidates, counted in
- * their step counters).  *best_ms_per_step (may be NULL) receives the time of
- * one step of the best candidate. */
+ * keep the fastest.  Each velocity-set group (set and Hermite order) with
+ * tiled solves has its own tile shape, cells per tile and tiles per grab.
+ * The groups run together in a chunk, so every candidate is timed on the
+ * whole chunk (two chunks after a warm-up chunk).  The search: the 11 tile
+ * shapes (linear tiles of 128, 256 or 512 consecutive nodes; rectangles 32 or
+ * 64 columns wide of 128, 256 or 512 nodes, or 128 wide of 256 or 512) for
+ * all groups at once; then, group by group, its own shape and its tiles per
+ * grab (1, 2, 4, 8 or 16), a change kept only when it saves more than 0.5 %;
+ * last the persistent grid at 1 or 1/2 of the occupancy limit.  The schedule
+ * decides which block updates a node, never the node's arithmetic: results
+ * are bitwise the same under every schedule.  The timed chunks advance the
+ * solves (3 chunks per candidate, counted in their step counters; 12 + 14 G
+ * candidates for G tiled groups from the default schedule).
+ * *best_ms_per_step (may be NULL) receives the time of one step of the best
+ * candidate. */
 int lbm_engine_autotune(lbm_engine* e, double* best_ms_per_step);
 
-/* Set or read the schedule the autotuner chooses.  tile_width: 0 for linear
- * tiles (consecutive nodes in row-major order), else 32, 64 or 128 columns (a
+/* Set or read a schedule.  slot: a used slot, addressing its velocity-set
+ * group, or -1 (set only) for every group.  tile_width: 0 for linear tiles
+ * (consecutive nodes in row-major order), else 32, 64 or 128 columns (a
  * solve whose Nx is not a multiple of it, or whose Ny is below the tile's
  * rows, takes linear tiles); tile_cells: nodes per tile, 128, 256 or 512;
  * grab: tiles taken per atomic grab, 1..64; grid_fraction: fraction of the
- * occupancy limit used for the persistent grid, (0, 1].  LBM_EINVAL for other
- * values or while launches are outstanding.  Takes effect at the next
- * lbm_engine_run or lbm_engine_launch.  Any pointer of the getter may be
- * NULL. */
-int lbm_engine_set_schedule(lbm_engine* e, int tile_width, int tile_cells, int grab,
+ * occupancy limit used for the persistent grid, (0, 1], common to all groups.
+ * LBM_EINVAL for other values, an unused slot, or while launches are
+ * outstanding.  Takes effect at the next lbm_engine_run or
+ * lbm_engine_launch.  Any output pointer of the getter may be NULL. */
+int lbm_engine_set_schedule(lbm_engine* e, int slot, int tile_width, int tile_cells, int grab,
                             double grid_fraction);
-int lbm_engine_get_schedule(const lbm_engine* e, int* tile_width, int* tile_cells, int* grab,
-                            double* grid_fraction);
+int lbm_engine_get_schedule(const lbm_engine* e, int slot, int* tile_width, int* tile_cells,
+                            int* grab, double* grid_fraction);
 
 /* Steps done by a slot and its status (LBM_OK or LBM_ENONFINITE). */
 int lbm_engine_info(lbm_engine* e, int slot, long* steps, int* status);

@@ -471,18 +471,21 @@ class Engine:
         check(_lib.lib().lbm_engine_autotune(self._h, ctypes.byref(ms)), "lbm_engine_autotune")
         return ms.value
 
-    def set_schedule(self, tile_width=0, tile_cells=128, grab=4, grid_fraction=1.0):
-        """Set the tiled kernel's schedule: tile_width 0 (linear tiles) or 32,
-        64, 128 columns; tile_cells 128, 256 or 512 nodes; grab tiles per
-        atomic grab; grid_fraction of the occupancy limit."""
-        check(_lib.lib().lbm_engine_set_schedule(self._h, int(tile_width), int(tile_cells), int(grab),
-                                                 float(grid_fraction)), "lbm_engine_set_schedule")
+    def set_schedule(self, tile_width=0, tile_cells=128, grab=4, grid_fraction=1.0, slot=-1):
+        """Set the tiled kernel's schedule of the velocity-set group of
+        ``slot`` (-1: every group): tile_width 0 (linear tiles) or 32, 64, 128
+        columns; tile_cells 128, 256 or 512 nodes; grab tiles per atomic grab;
+        grid_fraction of the occupancy limit (common to all groups)."""
+        check(_lib.lib().lbm_engine_set_schedule(self._h, int(slot), int(tile_width), int(tile_cells),
+                                                 int(grab), float(grid_fraction)),
+              "lbm_engine_set_schedule")
 
-    def schedule(self):
-        """The current schedule as a dict (the autotuner's choice after autotune)."""
+    def schedule(self, slot):
+        """The schedule of the velocity-set group of ``slot`` as a dict (the
+        autotuner's choice after autotune)."""
         tw, tc, g = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
         f = ctypes.c_double(0)
-        check(_lib.lib().lbm_engine_get_schedule(self._h, ctypes.byref(tw), ctypes.byref(tc),
+        check(_lib.lib().lbm_engine_get_schedule(self._h, int(slot), ctypes.byref(tw), ctypes.byref(tc),
                                                  ctypes.byref(g), ctypes.byref(f)),
               "lbm_engine_get_schedule")
         return {"tile_width": tw.value, "tile_cells": tc.value, "grab": g.value,

@@ -93,9 +93,9 @@ SIGNATURES = {
     "lbm_engine_wait": (ctypes.c_int, [ctypes.c_void_p, c_double_p]),
     "lbm_engine_autotune": (ctypes.c_int, [ctypes.c_void_p, c_double_p]),
     "lbm_engine_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                               ctypes.c_int, ctypes.c_double]),
-    "lbm_engine_get_schedule": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p, c_int_p,
-                                               c_double_p]),
+                                               ctypes.c_int, ctypes.c_int, ctypes.c_double]),
+    "lbm_engine_get_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p, c_int_p,
+                                               c_int_p, c_double_p]),
     "lbm_engine_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_long_p, c_int_p]),
     "lbm_engine_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p, c_double_p,
                                           c_double_p]),

@@ -44,13 +44,15 @@ struct EngineTile {
 };
 
 // Registers per thread allowed beyond the populations' share (min_blocks_for),
-// chosen per set from ptxas's spill report: the tile loop's addresses and flags
-// need ~12; with the solve's constants read from shared memory the 53-velocity
-// set fits 96 registers (20 warps per SM), while the 48-velocity set still
-// spills there and keeps 24.
+// chosen per set from ptxas's spill report and measured throughput: with the
+// solve's constants read from shared memory the 53-velocity set fits 96
+// registers (20 warps per SM); the 48-velocity set spills there and keeps 24
+// extra, the 40-velocity set 12; sets of at most 16 pairs take 6 (the
+// 33-velocity set at 72 registers, 28 warps per SM, a 16-byte spill: 3 %
+// faster than 80 registers without one).
 template <class SET>
 constexpr int engine_extra_regs() {
-    return SET::R + 2 * SET::P == 53 ? 0 : (SET::P > 20 ? 24 : 12);
+    return SET::R + 2 * SET::P == 53 ? 0 : (SET::P > 20 ? 24 : (SET::P > 16 ? 12 : 6));
 }
 
 // Moments, equilibrium, force and relaxation of one node (register values

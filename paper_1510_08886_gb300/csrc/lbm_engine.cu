@@ -3,8 +3,8 @@
 // that can be added and removed between chunks, per-velocity-set work lists
 // (bundles of channels small enough to run a whole chunk in shared memory,
 // tiles of the others), CUDA-graph capture of a chunk of time steps plus the
-// per-solve reductions, and an autotuner of the persistent grid size and the
-// tiles taken per grab.  Storage fp64 (fp64 arithmetic), fp32, fp16 or bf16
+// per-solve reductions, and an autotuner of each velocity set's tile shape,
+// cells per tile and tiles per grab and of the persistent grid.  Storage fp64 (fp64 arithmetic), fp32, fp16 or bf16
 // (fp32 arithmetic); the device slot records are EngineSolve<double> for fp64
 // and EngineSolve<float> otherwise.
 #include <algorithm>
@@ -175,9 +175,10 @@ struct lbm_engine {
     int pending = 0, head = 0;                 // outstanding launches, oldest one
     int K = 100;
     double bps_factor = 1.0;   // fraction of the occupancy limit used for the grid
-    int grab = 4;              // tiles taken per atomic grab
-    int tile_tws = 0;          // tile width 2^tws columns (0: linear tiles)
-    int tile_m = 1;            // tile of tile_m x 128 nodes
+    // schedule of each group's tiled launches
+    int grab[kGroups];         // tiles taken per atomic grab
+    int tile_tws[kGroups];     // tile width 2^tws columns (0: linear tiles)
+    int tile_m[kGroups];       // tiles of tile_m x 128 nodes
     int sms = 0;
     bool tiles_dirty = true, graph_dirty = true;
     // resident chunks
@@ -324,13 +325,13 @@ int rebuild_tiles(lbm_engine* e) {
                 res.push_back(s);
                 continue;
             }
-            const int Nx = sl.spec.Nx, Ny = sl.spec.Ny, cells = e->tile_m * lbm::kBlock;
-            const int tw = e->tile_tws ? 1 << e->tile_tws : 0, th = tw ? cells / tw : 0;
+            const int Nx = sl.spec.Nx, Ny = sl.spec.Ny, cells = e->tile_m[g] * lbm::kBlock;
+            const int tw = e->tile_tws[g] ? 1 << e->tile_tws[g] : 0, th = tw ? cells / tw : 0;
             if (tw && Nx % tw == 0 && Ny >= th) {
                 // at most 2 Nx Ny / cells tiles (Ny >= th)
                 for (int y0 = 0; y0 < Ny; y0 += th)
                     for (int x0 = 0; x0 < Nx; x0 += tw)
-                        t.push_back({s, y0 * Nx + x0, e->tile_tws});
+                        t.push_back({s, y0 * Nx + x0, e->tile_tws[g]});
             } else {
                 for (int c0 = 0; c0 < Nx * Ny; c0 += cells)
                     t.push_back({s, c0, 0});
@@ -458,8 +459,8 @@ int enqueue_chunk(lbm_engine* e) {
             L.seed = e->d_seed;
             L.parity = i & 1;
             L.emit = i == e->K - 1 ? 1 : (i == e->K - 2 ? 2 : 0);
-            L.chunk = e->grab;
-            L.lm = e->tile_m == 4 ? 2 : e->tile_m - 1;
+            L.chunk = e->grab[w.g];
+            L.lm = e->tile_m[w.g] == 4 ? 2 : e->tile_m[w.g] - 1;
             L.grid = w.grid;
             const int set = w.g / 3, N = w.g % 3 + 2;
             err = e->precision == LBM_FP16   ? lbm::engine_step_half(set, N, L, ts)
@@ -644,7 +645,12 @@ int lbm_engine_create(int precision, int max_solves, void* arena, size_t arena_b
     e->d_rcounters = reinterpret_cast<int*>(e->base + o_rcounters);
     e->d_bundles = reinterpret_cast<lbm::ResBundle*>(e->base + o_bundles);
     e->d_chans = reinterpret_cast<lbm::ResChannel*>(e->base + o_chans);
-    for (int g = 0; g < kGroups; ++g) e->res_occ[g] = -1;
+    for (int g = 0; g < kGroups; ++g) {
+        e->res_occ[g] = -1;
+        e->grab[g] = 4;
+        e->tile_tws[g] = 0;
+        e->tile_m[g] = 1;
+    }
     e->d_counters = reinterpret_cast<int*>(e->base + o_counters);
     e->d_seed = reinterpret_cast<unsigned*>(e->base + o_seed);
     e->d_tiles = reinterpret_cast<lbm::EngineTile*>(e->base + o_tiles);
@@ -869,8 +875,10 @@ int time_schedule(lbm_engine* e, cudaEvent_t a, cudaEvent_t b, float* ms) {
 
 }  // namespace
 
-// Coordinate search: the tile shape and cells per tile at the current grid and
-// grab, then the grid fraction and grab at the best shape.
+// Coordinate search over the tiled groups' schedules (groups run together in
+// a chunk, so each candidate is timed on the whole chunk): one tile shape and
+// cells per tile for all groups, then per group its own shape and its grab,
+// last the grid fraction.
 int lbm_engine_autotune(lbm_engine* e, double* best_ms_per_step) {
     if (!e || e->pending) return LBM_EINVAL;
     int rc = prepare(e);
@@ -878,69 +886,141 @@ int lbm_engine_autotune(lbm_engine* e, double* best_ms_per_step) {
     if (e->plan.empty()) return LBM_OK;
     static const int shapes[][2] = {{0, 1}, {0, 2}, {0, 4}, {5, 1}, {5, 2}, {5, 4},
                                     {6, 1}, {6, 2}, {6, 4}, {7, 2}, {7, 4}};
-    const double factors[] = {1.0, 0.5};
     const int grabs[] = {1, 2, 4, 8, 16};
-    double best = HUGE_VAL, bf = e->bps_factor;
-    int bg = e->grab, btws = e->tile_tws, bm = e->tile_m;
+    std::vector<int> tiled;
+    for (const GroupWork& w : e->plan)
+        if (w.tiled) tiled.push_back(w.g);
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess) return LBM_ECUDA;
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return LBM_ECUDA; }
-    for (const auto& sh : shapes) {
-        e->tile_tws = sh[0];
-        e->tile_m = sh[1];
-        e->tiles_dirty = true;
-        e->graph_dirty = true;
-        float ms = 0.f;
-        if ((rc = time_schedule(e, a, b, &ms))) break;
-        if (ms < best) { best = ms; btws = sh[0]; bm = sh[1]; }
-    }
-    e->tile_tws = btws;
-    e->tile_m = bm;
-    e->tiles_dirty = true;
+    float best = HUGE_VALF, ms = 0.f;
+    // the current schedule first
     e->graph_dirty = true;
-    for (double f : factors) {
-        if (rc) break;
-        for (int g : grabs) {
-            e->bps_factor = f;
-            e->grab = g;
-            e->graph_dirty = true;
-            float ms = 0.f;
+    rc = time_schedule(e, a, b, &best);
+    // one shape for every tiled group
+    if (!tiled.empty()) {
+        const int tws0 = e->tile_tws[tiled[0]], m0 = e->tile_m[tiled[0]];
+        int btws = tws0, bm = m0;
+        for (const auto& sh : shapes) {
+            if (rc) break;
+            if (sh[0] == tws0 && sh[1] == m0) continue;
+            for (int g : tiled) {
+                e->tile_tws[g] = sh[0];
+                e->tile_m[g] = sh[1];
+            }
+            e->tiles_dirty = e->graph_dirty = true;
             if ((rc = time_schedule(e, a, b, &ms))) break;
-            if (ms < best) { best = ms; bf = f; bg = g; }
+            if (ms < best) {
+                best = ms;
+                btws = sh[0];
+                bm = sh[1];
+            }
         }
+        for (int g : tiled) {
+            e->tile_tws[g] = btws;
+            e->tile_m[g] = bm;
+        }
+        e->tiles_dirty = e->graph_dirty = true;
+    }
+    // then each group's own shape and grab, a change kept only if it saves
+    // more than 0.5 % (the timing noise of two chunks)
+    for (int g : tiled) {
+        const int tws0 = e->tile_tws[g], m0 = e->tile_m[g];   // timed already
+        int btws = tws0, bm = m0;
+        for (const auto& sh : shapes) {
+            if (rc) break;
+            if (sh[0] == tws0 && sh[1] == m0) continue;
+            const int otws = e->tile_tws[g], om = e->tile_m[g];
+            e->tile_tws[g] = sh[0];
+            e->tile_m[g] = sh[1];
+            e->tiles_dirty = e->graph_dirty = true;
+            if ((rc = time_schedule(e, a, b, &ms))) break;
+            if (ms < 0.995f * best) {
+                best = ms;
+                btws = sh[0];
+                bm = sh[1];
+            } else {
+                e->tile_tws[g] = otws;
+                e->tile_m[g] = om;
+            }
+        }
+        e->tile_tws[g] = btws;
+        e->tile_m[g] = bm;
+        e->tiles_dirty = e->graph_dirty = true;
+        const int g0 = e->grab[g];     // timed already
+        int bg = g0;
+        for (int gr : grabs) {
+            if (rc) break;
+            if (gr == g0) continue;
+            e->grab[g] = gr;
+            e->graph_dirty = true;
+            if ((rc = time_schedule(e, a, b, &ms))) break;
+            if (ms < 0.995f * best) {
+                best = ms;
+                bg = gr;
+            } else {
+                e->grab[g] = bg;
+            }
+        }
+        e->grab[g] = bg;
+        e->graph_dirty = true;
+    }
+    if (!rc) {
+        const double bf = e->bps_factor;
+        e->bps_factor = bf == 1.0 ? 0.5 : 1.0;
+        e->graph_dirty = true;
+        rc = time_schedule(e, a, b, &ms);
+        if (!rc && ms >= 0.995f * best) e->bps_factor = bf;
+        if (!rc && ms < 0.995f * best) best = ms;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (rc) return rc;
-    e->bps_factor = bf;
-    e->grab = bg;
     e->graph_dirty = true;
     rc = prepare(e);
     if (best_ms_per_step) *best_ms_per_step = best / (2.0 * e->K);
     return rc;
 }
 
-int lbm_engine_set_schedule(lbm_engine* e, int tile_width, int tile_cells, int grab,
+namespace {
+
+bool slot_group(const lbm_engine* e, int slot, int* g) {
+    if (slot < 0 || slot >= e->max_slots || !e->slots[slot].used) return false;
+    *g = e->slots[slot].group;
+    return true;
+}
+
+}  // namespace
+
+int lbm_engine_set_schedule(lbm_engine* e, int slot, int tile_width, int tile_cells, int grab,
                             double grid_fraction) {
     if (!e || e->pending) return LBM_EINVAL;
     if (tile_width != 0 && tile_width != 32 && tile_width != 64 && tile_width != 128) return LBM_EINVAL;
     if (tile_cells != 128 && tile_cells != 256 && tile_cells != 512) return LBM_EINVAL;
     if (grab < 1 || grab > 64 || !(grid_fraction > 0.0 && grid_fraction <= 1.0)) return LBM_EINVAL;
-    e->tile_tws = tile_width == 0 ? 0 : (tile_width == 32 ? 5 : (tile_width == 64 ? 6 : 7));
-    e->tile_m = tile_cells / lbm::kBlock;
-    e->grab = grab;
+    int g0 = 0, g1 = kGroups;
+    if (slot != -1) {
+        if (!slot_group(e, slot, &g0)) return LBM_EINVAL;
+        g1 = g0 + 1;
+    }
+    for (int g = g0; g < g1; ++g) {
+        e->tile_tws[g] = tile_width == 0 ? 0 : (tile_width == 32 ? 5 : (tile_width == 64 ? 6 : 7));
+        e->tile_m[g] = tile_cells / lbm::kBlock;
+        e->grab[g] = grab;
+    }
     e->bps_factor = grid_fraction;
     e->tiles_dirty = true;
     e->graph_dirty = true;
     return LBM_OK;
 }
 
-int lbm_engine_get_schedule(const lbm_engine* e, int* tile_width, int* tile_cells, int* grab,
+int lbm_engine_get_schedule(const lbm_engine* e, int slot, int* tile_width, int* tile_cells, int* grab,
                             double* grid_fraction) {
-    if (!e) return LBM_EINVAL;
-    if (tile_width) *tile_width = e->tile_tws ? 1 << e->tile_tws : 0;
-    if (tile_cells) *tile_cells = e->tile_m * lbm::kBlock;
-    if (grab) *grab = e->grab;
+    int g = 0;
+    if (!e || !slot_group(e, slot, &g)) return LBM_EINVAL;
+    if (tile_width) *tile_width = e->tile_tws[g] ? 1 << e->tile_tws[g] : 0;
+    if (tile_cells) *tile_cells = e->tile_m[g] * lbm::kBlock;
+    if (grab) *grab = e->grab[g];
     if (grid_fraction) *grid_fraction = e->bps_factor;
     return LBM_OK;
 }

@@ -173,6 +173,6 @@ def test_engine_schedule_rejects_a_null_engine(L):
     lib = L.lib()
     tw, tc, g = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
     f = ctypes.c_double(0.0)
-    assert lib.lbm_engine_set_schedule(None, 32, 256, 4, 1.0) == L.LBM_EINVAL
-    assert lib.lbm_engine_get_schedule(None, ctypes.byref(tw), ctypes.byref(tc), ctypes.byref(g),
+    assert lib.lbm_engine_set_schedule(None, -1, 32, 256, 4, 1.0) == L.LBM_EINVAL
+    assert lib.lbm_engine_get_schedule(None, 0, ctypes.byref(tw), ctypes.byref(tc), ctypes.byref(g),
                                        ctypes.byref(f)) == L.LBM_EINVAL

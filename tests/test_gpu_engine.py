@@ -134,11 +134,15 @@ def test_autotune_keeps_results_exact():
     ms = a.autotune()
     assert ms > 0
     steps = a.info(sa[0])[0]
-    # 11 tile shapes + 2 grid fractions x 5 grabs, 3 chunks of 10 each
-    assert steps == 63 * 10
-    sched = a.schedule()
-    assert sched["tile_width"] in (0, 32, 64, 128) and sched["tile_cells"] in (128, 256, 512)
-    assert 1 <= sched["grab"] <= 16 and sched["grid_fraction"] in (0.5, 1.0)
+    # two tiled groups (D2V33 N=4 at 256 x 40, D3V107xz N=3 at 64 x 33; the
+    # one-column channels are resident): the current schedule, 10 more shapes
+    # for both groups, per group 10 more shapes and 4 more grabs, then the
+    # other grid fraction; 3 chunks of 10 steps each
+    assert steps == (12 + 14 * 2) * 3 * 10
+    for slot in sa:
+        sched = a.schedule(slot)
+        assert sched["tile_width"] in (0, 32, 64, 128) and sched["tile_cells"] in (128, 256, 512)
+        assert sched["grab"] in (1, 2, 4, 8, 16) and sched["grid_fraction"] in (0.5, 1.0)
     a.run(1)
     b.run(steps // 10 + 1)
     for x, y, spec in zip(sa, sb, MIX[:4]):
@@ -392,10 +396,16 @@ def test_schedules_bitwise_equal(precision):
     engines, slots = [], []
     for tw, tc, grab, frac in SCHEDULES:
         eng = lbm.Engine(precision, max_solves=16, arena_bytes=128 << 20, chunk=20, resident=False)
+        sl = [_add(eng, s, seed=31 + i) for i, s in enumerate(SCHEDULE_MIX)]
         eng.set_schedule(tw, tc, grab, frac)
-        assert eng.schedule() == {"tile_width": tw, "tile_cells": tc, "grab": grab,
-                                  "grid_fraction": frac}
-        slots.append([_add(eng, s, seed=31 + i) for i, s in enumerate(SCHEDULE_MIX)])
+        # per group: the first D2V33 solve's group also takes a second schedule
+        other = SCHEDULES[(SCHEDULES.index((tw, tc, grab, frac)) + 3) % len(SCHEDULES)]
+        eng.set_schedule(*other[:3], frac, slot=sl[0])
+        for i in range(len(sl)):
+            want = other[:3] if SCHEDULE_MIX[i][:2] == ("D2V33", 4) else (tw, tc, grab)
+            assert eng.schedule(sl[i]) == {"tile_width": want[0], "tile_cells": want[1],
+                                           "grab": want[2], "grid_fraction": frac}
+        slots.append(sl)
         engines.append(eng)
     res = [eng.run(2).copy() for eng in engines]
     for j in range(1, len(engines)):
@@ -419,4 +429,12 @@ def test_schedule_validates():
                 (0, 128, 65, 1.0), (0, 128, 4, 0.0), (0, 128, 4, 1.5)]:
         with pytest.raises(lbm.LBMError):
             eng.set_schedule(*bad)
+    # a slot must be in use
+    with pytest.raises(lbm.LBMError):
+        eng.set_schedule(0, 128, 4, 1.0, slot=0)
+    with pytest.raises(lbm.LBMError):
+        eng.schedule(1)
+    s = _add(eng, ("D2V16", 3, 1, 64, 0.1), seed=1)
+    eng.set_schedule(32, 256, 2, 0.5, slot=s)
+    assert eng.schedule(s) == {"tile_width": 32, "tile_cells": 256, "grab": 2, "grid_fraction": 0.5}
     eng.close()
