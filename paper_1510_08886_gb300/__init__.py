@@ -401,13 +401,6 @@ class Engine:
         check(_lib.lib().lbm_engine_set_chunk(self._h, int(steps)), "lbm_engine_set_chunk")
         self.chunk = int(steps)
 
-    def average(self, n, every=1):
-        """Advance n steps and leave in the moment fields the mean of the
-        moments of every `every`-th step (lbm_average): the observables then
-        report time averages, the steady state of 16-bit storage."""
-        check(_lib.lib().lbm_average(self._h, int(n), int(every)), "lbm_average")
-        return self
-
     def set_resident(self, enable):
         check(_lib.lib().lbm_engine_set_resident(self._h, int(bool(enable))),
               "lbm_engine_set_resident")
