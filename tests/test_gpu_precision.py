@@ -9,9 +9,10 @@ rounds every store stochastically, so its state never stops moving (rounding
 noise ~1e-7 per step): after 20,000 steps it is in a statistical steady
 state, and its observables are the time averages of the next 60,000 steps
 (lbm_average), which meet the same 1e-4 target.  bf16 storage (8 mantissa
-bits) is outside the 1e-4 target set: its averaged errors reach a few 1e-4
-(measured table in the design notes), so only its short-transient parity is
-tested here, at a tolerance set by its resolution.
+bits) is noisier: averages over 30,000 steps still err by a few 1e-4, but
+the error falls with the window (the rounding is unbiased), and averages over
+1,920,000 steps after the same 20,000-step warm-up meet 1e-4 at every point
+(max 5.1e-5 / 5.9e-5 measured).
 """
 import numpy as np
 import pytest
@@ -22,7 +23,7 @@ from lbm_inputs import kn_sweep, rho_field
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": (1e-4, 1e-4), "fp16": (1e-4, 1e-4)}
+TOL = {"fp32": (1e-4, 1e-4), "fp16": (1e-4, 1e-4), "bf16": (1e-4, 1e-4)}
 _REF = {}
 
 
@@ -74,6 +75,16 @@ def test_fp16_storage_kn_sweep_time_averaged(Kn):
     m, u = _gpu_averaged(Kn, "fp16")
     assert abs(m / m_o - 1) < TOL["fp16"][0]
     assert abs(u / u_o - 1) < TOL["fp16"][1]
+
+
+@pytest.mark.parametrize("Kn", list(kn_sweep(8)))
+def test_bf16_storage_kn_sweep_long_time_average(Kn):
+    """bf16 meets the 1e-4 target as an average over 1,920,000 steps (about
+    12 s per point on the 1 x 64 channel)."""
+    m_o, u_o = _oracle_steady(Kn)
+    m, u = _gpu_averaged(Kn, "bf16", window=1920000)
+    assert abs(m / m_o - 1) < TOL["bf16"][0]
+    assert abs(u / u_o - 1) < TOL["bf16"][1]
 
 
 def test_average_of_a_steady_state_is_the_state():
