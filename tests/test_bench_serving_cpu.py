@@ -42,3 +42,26 @@ def test_beyond_first_check_rates_and_gate():
 def test_beyond_first_check_empty():
     out = bench._beyond_first_check({}, {}, wall=1.0)
     assert out["requests"] == 0 and out["solves_per_s"] == 0.0 and math.isnan(out["p50_s"])
+
+
+def test_first_check_du_is_the_bulk_acceleration():
+    """Why tol = 1e-6 requests can stop at the first check: the walls reach at
+    most max|e_y| rows per step, so after 100 steps the centre of a channel of
+    more than 2 x 300 rows is still uniform bulk, accelerating by exactly g dt
+    per step (dt = 1/(Ny c)), and max|du| there is g dt.  On the oracle,
+    D2V16, N = 3."""
+    import numpy as np
+    import oracle
+    from lbm_inputs.tables import DVM_TABLES
+    c = DVM_TABLES["D2V16"]["c"]
+    for Ny, Kn in ((768, 0.02), (1024, 0.3)):
+        g = oracle.force_for_mach(Kn)
+        ch = oracle.channel("D2V16", 3, 1, Ny, Kn, g)
+        ch.init()
+        ch.step(99)
+        u0 = ch.moments()[1].copy()
+        ch.step(1)
+        du = np.abs(ch.moments()[1] - u0)
+        mid = du.reshape(Ny)[Ny // 2]
+        assert abs(mid / (g / (Ny * c)) - 1) < 1e-9
+        assert abs(du.max() / (g / (Ny * c)) - 1) < 1e-9
