@@ -17,7 +17,7 @@ OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "liblbm.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["k_fp64.cu", "k_cluster.cu", "k_fp32.cu", "k_fp16.cu", "engine_fp32.cu", "engine_fp16.cu",
+SOURCES = ["k_fp64.cu", "k_cluster.cu", "k_fp32.cu", "k_fp16.cu", "k_bf16.cu", "engine_fp32.cu", "engine_fp16.cu",
            "engine_fp64.cu", "engine_res_fp64.cu",
            "engine_bf16.cu", "engine_res_fp32.cu", "engine_res_half.cu", "engine_res_bf16.cu",
            "lbm_engine.cu", "lbm_api.cu", "lbm_noalloc.cu", "peak_probe.cu", "dvm.cpp", "dvm_gen.cpp"]

@@ -1,20 +1,28 @@
-// 16-bit storage instantiations (IEEE half and bfloat16) of the stream-collide
-// kernels: populations stored as h = (fbar - w) / (w S), arithmetic in fp32,
-// wall fluxes and moments in fp64.  Also the two state-wide helpers of the
-// per-solve scale S: the max |h| reduction and the power-of-2 rescale.
+// 16-bit storage instantiations of the stream-collide kernels: populations
+// stored as h = (fbar - w) / (w S), arithmetic in fp32, wall fluxes and
+// moments in fp64.  IEEE half here; bfloat16 in k_bf16.cu (its own
+// translation unit, compiled in parallel), reached through the same two
+// launchers.  Also the two state-wide helpers of the per-solve scale S: the
+// max |h| reduction and the power-of-2 rescale.
 #include "lbm_kernels.cuh"
 
 namespace lbm {
 
+// k_bf16.cu
+cudaError_t launch_step_bf16_only(const KParams<float>& k, int N, const void* src, void* dst,
+                                  const DevBufs& b, cudaStream_t st);
+cudaError_t launch_init_bf16_only(const KParams<float>& k, int N, const double* rho0, void* dst,
+                                  const DevBufs& b, cudaStream_t st);
+
 cudaError_t launch_step_fp16(const KParams<float>& k, int N, bool bf16, const void* src, void* dst,
                              const DevBufs& b, cudaStream_t st) {
-    return bf16 ? launch_step_t<__nv_bfloat16, float>(k, N, src, dst, b, st)
+    return bf16 ? launch_step_bf16_only(k, N, src, dst, b, st)
                 : launch_step_t<__half, float>(k, N, src, dst, b, st);
 }
 
 cudaError_t launch_init_fp16(const KParams<float>& k, int N, bool bf16, const double* rho0,
                              void* dst, const DevBufs& b, cudaStream_t st) {
-    return bf16 ? launch_init_t<__nv_bfloat16, float>(k, N, rho0, dst, b, st)
+    return bf16 ? launch_init_bf16_only(k, N, rho0, dst, b, st)
                 : launch_init_t<__half, float>(k, N, rho0, dst, b, st);
 }
 
